@@ -1,0 +1,302 @@
+"""Benchmark: single-graph bitruss decomposition on the 2M-edge skewed workload.
+
+A step is one full pass of the path -- rank-ordered CSR build, wedge count
+with support attribution, BE-Index emit and batch peeling -- over one
+synthetic graph (|U|=200,000, |L|=80,000, m=2,000,000, exponents 2.1/2.4,
+degree cap 20,000).  The timed value uses device-resident edges and outputs;
+``e2e`` repeats the step through the C ABI with host buffers (host->device
+edge copy and device->host support/phi copy inside the timed region).
+
+Multi-GPU: one process per GPU (torchrun); each rank decomposes its own
+replica, no collective on the data path (replicas only, weak scaling).
+
+``--impl reference`` times the CPU oracle instead (bounded vertex sample of
+the same workload per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="chunglu-200k-80k-2M-cap20k", nU=200000, nL=80000, m=2000000, gammaU=2.1,
+                gammaL=2.4, cap=20000, seed=2)
+METRIC = "edges decomposed/s"
+UNIT = "edges/s"
+CPU_SAMPLE_FRAC = 0.3   # vertex-induced sample for the oracle baseline
+REF_SAMPLE_FRAC = 0.2   # per-step sample for the reference arm
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_bytes(p):
+    """Per-launch algorithmic bytes of the count and emit kernels (figures per
+    wedge / bloom wedge / bloom / edge as stated in the design notes)."""
+    W, W2, NB, m = p["n_wedges"], p["n_bloom_wedges"], p["n_blooms"], p["n_edges"]
+    count = 12 * W + 8 * W2 + 20 * m
+    emit = 8 * W + 20 * W2 + 12 * NB
+    return {"count": count, "emit": emit}
+
+
+def run_reference(args):
+    import oracle
+    from paper_2001_06111_gb300 import synth
+
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    g = synth.chunglu(WORKLOAD["nU"], WORKLOAD["nL"], WORKLOAD["m"], WORKLOAD["gammaU"],
+                      WORKLOAD["gammaL"], seed=WORKLOAD["seed"], cap=WORKLOAD["cap"])
+    sample = synth.vertex_sample(g, REF_SAMPLE_FRAC, 7)
+    for _ in range(args.warmup):
+        oracle.bitruss(sample.edges, sample.nU, sample.nL)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.bitruss(sample.edges, sample.nU, sample.nL)
+    dt = time.perf_counter() - t0
+    value = sample.m * args.steps / dt
+    desc = (f"{int(REF_SAMPLE_FRAC * 100)}% vertex-induced sample of {WORKLOAD['name']} "
+            f"({sample.m} edges) per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "sample": desc, "parallelism": "cpu oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline():
+    import oracle
+    from paper_2001_06111_gb300 import synth
+
+    g = synth.chunglu(WORKLOAD["nU"], WORKLOAD["nL"], WORKLOAD["m"], WORKLOAD["gammaU"],
+                      WORKLOAD["gammaL"], seed=WORKLOAD["seed"], cap=WORKLOAD["cap"])
+    s = synth.vertex_sample(g, CPU_SAMPLE_FRAC, 7)
+    t0 = time.perf_counter()
+    oracle.bitruss(s.edges, s.nU, s.nL)
+    dt = time.perf_counter() - t0
+    return {"value": s.m / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": (f"{int(CPU_SAMPLE_FRAC * 100)}% vertex-induced sample of {WORKLOAD['name']}"
+                       f" ({s.m} edges), support count on all cores, peeling single-threaded"),
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    ws, rank, local = dist_env()
+    # the CPU baseline runs before the first CUDA call (rank 0, N=1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    import torch
+    from paper_2001_06111_gb300 import bitruss as bt
+    from paper_2001_06111_gb300 import build, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    g = synth.chunglu(WORKLOAD["nU"], WORKLOAD["nL"], WORKLOAD["m"], WORKLOAD["gammaU"],
+                      WORKLOAD["gammaL"], seed=WORKLOAD["seed"], cap=WORKLOAD["cap"])
+    m = g.m
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    h = bt.bt_create(local, stream)
+    bt.bt_profile_enable(h, True)
+    d_edges = torch.from_numpy(g.edges).cuda()
+    d_sup = torch.empty(m, dtype=torch.int64, device="cuda")
+    d_phi = torch.empty(m, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        bt.bt_decompose(h, d_edges, g.nU, g.nL, support_out=d_sup, phi_out=d_phi)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    step_ms = []
+    profs = []
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 between timed steps (outside the timed events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        profs.append(bt.bt_profile_read(h))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * m * args.steps / (total_ms / 1e3)
+
+    # end-to-end through the C ABI with host buffers
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sup_h, phi_h, _ = bt.bt_decompose(h, g.edges, g.nU, g.nL)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = ws * m * e2e_steps / e2e_s
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    p0 = profs[-1]
+    med = lambda key: statistics.median(p[key] for p in profs)  # noqa: E731
+    ab = algorithmic_bytes(p0)
+    peak, peak_kind = load_peaks()
+    kern = {"count": med("count_ms"), "emit": med("emit_ms")}
+    dom = max(kern, key=kern.get)
+    achieved = ab[dom] / (kern[dom] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "nU": g.nU, "nL": g.nL, "m": m,
+                   "exponents": [WORKLOAD["gammaU"], WORKLOAD["gammaL"]], "degree_cap": WORKLOAD["cap"],
+                   "seed": WORKLOAD["seed"], "parallelism": f"replicas x{ws}",
+                   "cache": "L2 flushed (256 MiB write) before every timed step"},
+        "wedges_per_s": p0["n_wedges"] / ((med("count_ms") + med("emit_ms")) / 1e3),
+        "phases_ms": {"csr": med("csr_ms"), "count": med("count_ms"), "emit": med("emit_ms"),
+                      "peel": med("peel_ms"), "call": med("total_ms")},
+        "work": {k: p0[k] for k in ("n_wedges", "n_bloom_wedges", "n_blooms", "rounds", "levels",
+                                    "support_updates")},
+        "roofline": {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes": ab[dom], "traffic": None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * m,
+                "d2h_bytes_per_step": 12 * m, "steps": e2e_steps},
+        "gpu_launches": int(sum(p["launches"] for p in profs)),
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * bitruss.h -- C ABI of the GB300 (sm_103a) bitruss decomposition library
+ * (libbitruss.so).
+ *
+ * Method: "Efficient Bitruss Decomposition for Large-scale Bipartite Graphs"
+ * (arXiv 2001.06111).  The library computes, for a bipartite graph
+ * G(U, L, E) given as an edge list,
+ *   support(e) -- the butterfly support of every edge (Section II, Defs. 2-3),
+ *                 counted by priority-obeyed wedge enumeration (Def. 10, Section IV-B,
+ *                 Alg. 3; vertex priority of Def. 7);
+ *   the BE-Index -- maximal priority-obeyed blooms with their bloom numbers,
+ *                 edge-bloom links and twin edges (Section IV-A, Defs. 8-9,
+ *                 built as in Alg. 3);
+ *   phi(e)     -- the bitruss number of every edge (Defs. 4-5), by
+ *                 level-synchronous batch peeling through the BE-Index
+ *                 (Section V-B, Alg. 5 with the <= k rule of Alg. 4).
+ *
+ * Conventions shared by all calls
+ *   - Edges: int32 pairs (u, v), row-major, 2*m values; u in [0, nU) names an
+ *     upper-layer vertex, v in [0, nL) a lower-layer vertex.  Edges must be
+ *     distinct.  Outputs are indexed like the input edges.
+ *   - Pointers are host pointers unless flags contain BT_DEVICE_PTRS, in which
+ *     case every edge/output pointer of that call is a device pointer on the
+ *     handle's device.  The caller owns all input and output memory; the
+ *     library never frees it and never keeps it past the call.
+ *   - Vertex ids: the paper orders equal-degree vertices by a global id with
+ *     every upper id above every lower id (Section II).  BT_TIE_LOWER_FIRST
+ *     puts the lower layer above instead (the reading under which the paper's
+ *     Fig. 6 index is reproduced).  Supports and bitruss numbers do not
+ *     depend on this choice; only the BE-Index layout does.
+ *   - Every call returns a bt_status.  On failure bt_last_error() describes
+ *     it; outputs are then unspecified.  No call throws or aborts.
+ *   - Calls on one handle are serialised by the caller (a handle is not
+ *     thread-safe); different handles may be used from different threads.
+ *   - All device work is issued on the handle's stream.  A call returns after
+ *     its results are in the caller's buffers (it synchronises that stream).
+ */
+#ifndef BITRUSS_H
+#define BITRUSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BT_OK = 0,
+    BT_ERR_ARG = 1,         /* null pointer, bad size or flag */
+    BT_ERR_RANGE = 2,       /* a vertex id outside [0,nU) / [0,nL) */
+    BT_ERR_DUP = 3,         /* the same edge appears twice */
+    BT_ERR_NOMEM = 4,       /* device allocation failed */
+    BT_ERR_OVERFLOW = 5,    /* a count exceeds its storage type (e.g. phi > 2^32-1) */
+    BT_ERR_NOCONVERGE = 6,  /* peeling exceeded its round limit */
+    BT_ERR_CUDA = 7,        /* a CUDA runtime call failed */
+    BT_ERR_STATE = 8        /* call needs state the handle does not hold */
+} bt_status;
+
+/* flags */
+#define BT_DEVICE_PTRS 0x1u      /* edge/output pointers are device pointers */
+#define BT_TIE_LOWER_FIRST 0x2u  /* lower-layer global ids above upper-layer ids */
+
+typedef struct bt_handle bt_handle;
+
+/* Sizes of a BE-Index (Section IV-A) and of the wedge work that built it. */
+typedef struct {
+    uint64_t n_wedges;        /* priority-obeyed wedges (Def. 10), W */
+    uint64_t n_bloom_wedges;  /* wedges inside a bloom (end pair count >= 2), W2 = links/2 */
+    uint64_t n_blooms;        /* maximal priority-obeyed blooms, |U(I)| */
+    uint64_t n_butterflies;   /* sum over blooms of C(k,2) = butterflies of G (Lemmas 1, 3) */
+    uint64_t index_bytes;     /* device bytes held by the index */
+} bt_index_stats;
+
+/* One bloom of the index copied out for inspection (bt_index_export). */
+typedef struct {
+    uint32_t k;               /* bloom number */
+    uint32_t first_pair;      /* index of its first twin pair in pairs_out */
+} bt_bloom_rec;
+
+/* Per-call peel statistics (filled by bt_decompose when stats != NULL). */
+typedef struct {
+    uint64_t rounds;          /* peeling rounds (batches S, Alg. 5 line 4) */
+    uint64_t levels;          /* distinct k values at which a batch was peeled */
+    uint64_t support_updates; /* edge-support decrements applied (Fig. 10's count) */
+    uint32_t phi_max;         /* largest bitruss number */
+    uint32_t reserved;
+} bt_peel_stats;
+
+/* Per-call profile (bt_profile_read): CUDA-event times of the phases of the
+ * last call on the handle, recorded on the handle's stream, and its kernel
+ * launch count.  A phase that did not run reads 0. */
+typedef struct {
+    float csr_ms;      /* degree, rank and rank-ordered CSR build */
+    float count_ms;    /* the wedge-count kernel (support attribution) */
+    float emit_ms;     /* the BE-Index emit kernel */
+    float peel_ms;     /* the whole peeling loop */
+    float total_ms;    /* the whole call, host staging included */
+    uint32_t reserved;
+    uint64_t launches; /* kernels this call launched */
+    uint64_t n_edges, n_vertices, n_wedges, n_bloom_wedges, n_blooms;
+    uint64_t rounds, levels, support_updates;
+} bt_profile;
+
+/*
+ * Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to issue work on, or NULL to let the handle create and own one.
+ * Errors: BT_ERR_ARG (h NULL), BT_ERR_CUDA (device unusable).
+ */
+int bt_create(bt_handle **h, int device, void *cuda_stream);
+
+/* Release the handle, its stream (if owned) and all device memory it holds. */
+int bt_destroy(bt_handle *h);
+
+/* Last error message of the handle ("" if none); valid until the next call. */
+const char *bt_last_error(const bt_handle *h);
+
+/*
+ * Butterfly support of every edge (Defs. 2-3; counted by priority-obeyed
+ * wedges as in Alg. 3, with Lemmas 2-3).
+ *   support_out: uint64[m], caller-allocated (host, or device with
+ *   BT_DEVICE_PTRS).
+ * Errors: BT_ERR_ARG, BT_ERR_RANGE, BT_ERR_DUP, BT_ERR_NOMEM, BT_ERR_CUDA.
+ * m == 0 returns BT_OK.
+ */
+int bt_count_support(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                     uint64_t *support_out, uint32_t flags);
+
+/*
+ * Build the BE-Index (Section IV, Alg. 3) and keep it resident on the device
+ * inside the handle (replacing any earlier index).  stats_out may be NULL.
+ * Errors: as bt_count_support, plus BT_ERR_OVERFLOW when the index has
+ * 2^32 or more twin pairs.
+ */
+int bt_build_index(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                   bt_index_stats *stats_out, uint32_t flags);
+
+/*
+ * Copy the resident index to host memory for inspection.  Any of the output
+ * pointers may be NULL to skip it; sizes come from bt_index_stats.
+ *   blooms_out:   bt_bloom_rec[n_blooms]  (blooms in index order)
+ *   pairs_out:    uint32[2 * n_bloom_wedges]: twin pair i is the edge ids
+ *                 (pairs_out[2i], pairs_out[2i+1]) = ((u,v), (v,w)) of one
+ *                 priority-obeyed wedge (u,v,w) of its bloom; the two edges
+ *                 are each other's twin (Def. 9).  Pairs of one bloom are
+ *                 contiguous, starting at first_pair.
+ *   edge_deg_out: uint32[m]: number of links of each edge, |N_I(e)|.
+ * Errors: BT_ERR_STATE (no index), BT_ERR_CUDA.
+ */
+int bt_index_export(bt_handle *h, bt_bloom_rec *blooms_out, uint32_t *pairs_out,
+                    uint32_t *edge_deg_out);
+
+/*
+ * Bitruss number of every edge (Defs. 4-5): counting, BE-Index build, then
+ * level-synchronous batch peeling (Alg. 5; every unassigned edge with
+ * support <= k is peeled in one batch, k = max(k, minimum support)).
+ *   support_out: uint64[m] or NULL -- the initial supports.
+ *   phi_out:     uint32[m].
+ *   stats:       may be NULL.
+ * Errors: as bt_build_index, plus BT_ERR_OVERFLOW (phi > 2^32-1) and
+ * BT_ERR_NOCONVERGE (round limit, which is m + 1 rounds).
+ */
+int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                 uint64_t *support_out, uint32_t *phi_out, bt_peel_stats *stats, uint32_t flags);
+
+/*
+ * Turn per-phase event timing on (on != 0) or off for later calls on h.
+ * Timing adds one event record per phase boundary and a final wait.
+ * Errors: BT_ERR_ARG, BT_ERR_CUDA.
+ */
+int bt_profile_enable(bt_handle *h, int on);
+
+/* Profile of the last bt_count_support / bt_build_index / bt_decompose call
+ * on h (zeros for phases it did not run, and times only when profiling was
+ * enabled).  Errors: BT_ERR_ARG. */
+int bt_profile_read(const bt_handle *h, bt_profile *out);
+
+/*
+ * Device bytes a bt_decompose of this graph needs (host computation, O(m)
+ * time; edges are host pointers).  It counts priority-obeyed wedges exactly,
+ * so the estimate for the BE-Index is an upper bound (every wedge assumed to
+ * lie in a bloom).
+ * Errors: BT_ERR_ARG, BT_ERR_RANGE.
+ */
+int bt_estimate_bytes(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
+                      uint64_t *bytes_out, uint64_t *wedges_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BITRUSS_H */

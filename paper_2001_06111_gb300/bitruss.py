@@ -1,0 +1,258 @@
+"""Thin ctypes binding of ``libbitruss.so`` (C ABI in include/bitruss.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Host inputs are numpy arrays; device inputs are CUDA torch tensors
+(their pointers are passed with ``BT_DEVICE_PTRS``).  Torch is used only to
+hold device memory and to name a stream.  If the library has not been built
+(or a symbol is missing) loading fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbitruss.so")
+
+BT_OK = 0
+BT_ERR_ARG = 1
+BT_ERR_RANGE = 2
+BT_ERR_DUP = 3
+BT_ERR_NOMEM = 4
+BT_ERR_OVERFLOW = 5
+BT_ERR_NOCONVERGE = 6
+BT_ERR_CUDA = 7
+BT_ERR_STATE = 8
+BT_DEVICE_PTRS = 0x1
+BT_TIE_LOWER_FIRST = 0x2
+
+EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_build_index",
+            "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
+            "bt_profile_read")
+
+
+class BitrussError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bitruss error {code}: {msg}")
+        self.code = code
+
+
+class IndexStats(ctypes.Structure):
+    _fields_ = [("n_wedges", ctypes.c_uint64), ("n_bloom_wedges", ctypes.c_uint64),
+                ("n_blooms", ctypes.c_uint64), ("n_butterflies", ctypes.c_uint64),
+                ("index_bytes", ctypes.c_uint64)]
+
+
+class BloomRec(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("first_pair", ctypes.c_uint32)]
+
+
+class PeelStats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("support_updates", ctypes.c_uint64), ("phi_max", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("csr_ms", ctypes.c_float), ("count_ms", ctypes.c_float),
+                ("emit_ms", ctypes.c_float), ("peel_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float), ("reserved", ctypes.c_uint32),
+                ("launches", ctypes.c_uint64), ("n_edges", ctypes.c_uint64),
+                ("n_vertices", ctypes.c_uint64), ("n_wedges", ctypes.c_uint64),
+                ("n_bloom_wedges", ctypes.c_uint64), ("n_blooms", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("support_updates", ctypes.c_uint64)]
+
+
+def _as_dict(s: ctypes.Structure) -> dict:
+    out = {}
+    for f, t in s._fields_:
+        if f == "reserved":
+            continue
+        v = getattr(s, f)
+        out[f] = float(v) if t is ctypes.c_float else int(v)
+    return out
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (build it first with ``paper_2001_06111_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"libbitruss.so not built at {path}; run paper_2001_06111_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name in EXPORTED:
+            if not hasattr(lib, name):
+                raise ImportError(f"libbitruss.so does not export {name}")
+        P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        lib.bt_create.argtypes = [ctypes.POINTER(P), I, P]
+        lib.bt_destroy.argtypes = [P]
+        lib.bt_last_error.argtypes = [P]
+        lib.bt_last_error.restype = ctypes.c_char_p
+        lib.bt_count_support.argtypes = [P, P, U64, U32, U32, P, U32]
+        lib.bt_build_index.argtypes = [P, P, U64, U32, U32, ctypes.POINTER(IndexStats), U32]
+        lib.bt_index_export.argtypes = [P, P, P, P]
+        lib.bt_decompose.argtypes = [P, P, U64, U32, U32, P, P, ctypes.POINTER(PeelStats), U32]
+        lib.bt_profile_enable.argtypes = [P, I]
+        lib.bt_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
+        lib.bt_estimate_bytes.argtypes = [P, U64, U32, U32, U32, ctypes.POINTER(U64),
+                                          ctypes.POINTER(U64)]
+        for name in EXPORTED:
+            if name != "bt_last_error":
+                getattr(lib, name).restype = I
+        _lib = lib
+        return lib
+
+
+class Handle:
+    """Owns a ``bt_handle*`` (device, stream and device-resident index)."""
+
+    def __init__(self, ptr: int, device: int):
+        self.ptr = ptr
+        self.device = device
+
+    def close(self):
+        if self.ptr:
+            load().bt_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _check(h, rc: int):
+    if rc != BT_OK:
+        msg = load().bt_last_error(h.ptr if h is not None else None)
+        raise BitrussError(rc, msg.decode() if msg else "")
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _edges_arg(edges):
+    """(pointer, m, flags, keepalive) for a numpy (host) or torch (device) edge list."""
+    if _is_torch(edges):
+        if not edges.is_cuda:
+            edges = edges.numpy()
+        else:
+            import torch
+            assert edges.dtype == torch.int32 and edges.is_contiguous() and edges.dim() == 2
+            return edges.data_ptr(), int(edges.shape[0]), BT_DEVICE_PTRS, edges
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    return e.ctypes.data, int(e.shape[0]), 0, e
+
+
+def _out(like_device, m, dtype_np, torch_dtype, given):
+    if given is not None:
+        ptr = given.data_ptr() if _is_torch(given) else given.ctypes.data
+        return given, ptr
+    if like_device is not None:
+        import torch
+        t = torch.empty(m, dtype=torch_dtype, device=like_device.device)
+        return t, t.data_ptr()
+    a = np.empty(m, dtype=dtype_np)
+    return a, a.ctypes.data
+
+
+def bt_create(device: int = 0, stream=None) -> Handle:
+    lib = load()
+    p = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.bt_create(ctypes.byref(p), device, s)
+    if rc != BT_OK:
+        raise BitrussError(rc, f"bt_create(device={device}) failed")
+    return Handle(p.value, device)
+
+
+def bt_count_support(h: Handle, edges, nU: int, nL: int, support_out=None, flags: int = 0):
+    ptr, m, f, keep = _edges_arg(edges)
+    import_dev = keep if f & BT_DEVICE_PTRS else None
+    sup, sptr = _out(import_dev, m, np.uint64, _torch_dtype("uint64"), support_out)
+    _check(h, load().bt_count_support(h.ptr, ptr, m, nU, nL, sptr, flags | f))
+    return sup
+
+
+def bt_build_index(h: Handle, edges, nU: int, nL: int, flags: int = 0) -> dict:
+    ptr, m, f, keep = _edges_arg(edges)
+    st = IndexStats()
+    _check(h, load().bt_build_index(h.ptr, ptr, m, nU, nL, ctypes.byref(st), flags | f))
+    return _as_dict(st)
+
+
+def bt_index_export(h: Handle, stats: dict, m: int):
+    """Return (bloom k u32[nb], bloom first pair u32[nb], pairs u32[w2,2], links per edge u32[m])."""
+    nb, w2 = stats["n_blooms"], stats["n_bloom_wedges"]
+    blooms = (BloomRec * max(nb, 1))()
+    pairs = np.empty((max(w2, 1), 2), dtype=np.uint32)
+    deg = np.empty(max(m, 1), dtype=np.uint32)
+    _check(h, load().bt_index_export(h.ptr, ctypes.addressof(blooms), pairs.ctypes.data,
+                                     deg.ctypes.data))
+    k = np.array([blooms[i].k for i in range(nb)], dtype=np.uint32)
+    first = np.array([blooms[i].first_pair for i in range(nb)], dtype=np.uint32)
+    return k, first, pairs[:w2], deg[:m]
+
+
+def bt_decompose(h: Handle, edges, nU: int, nL: int, support_out=None, phi_out=None,
+                 flags: int = 0, want_support: bool = True):
+    """Return (support u64[m] or None, phi u32[m], stats dict)."""
+    ptr, m, f, keep = _edges_arg(edges)
+    dev = keep if f & BT_DEVICE_PTRS else None
+    sup, sptr = (None, None)
+    if want_support or support_out is not None:
+        sup, sptr = _out(dev, m, np.uint64, _torch_dtype("uint64"), support_out)
+    phi, pptr = _out(dev, m, np.uint32, _torch_dtype("uint32"), phi_out)
+    st = PeelStats()
+    _check(h, load().bt_decompose(h.ptr, ptr, m, nU, nL, sptr, pptr, ctypes.byref(st), flags | f))
+    return sup, phi, _as_dict(st)
+
+
+def bt_profile_enable(h: Handle, on: bool = True):
+    _check(h, load().bt_profile_enable(h.ptr, 1 if on else 0))
+
+
+def bt_profile_read(h: Handle) -> dict:
+    p = Profile()
+    _check(h, load().bt_profile_read(h.ptr, ctypes.byref(p)))
+    return _as_dict(p)
+
+
+def bt_estimate_bytes(edges, nU: int, nL: int, flags: int = 0):
+    """Return (device bytes needed, priority-obeyed wedges) for a host edge list."""
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    b = ctypes.c_uint64()
+    w = ctypes.c_uint64()
+    rc = load().bt_estimate_bytes(e.ctypes.data, e.shape[0], nU, nL, flags, ctypes.byref(b),
+                                  ctypes.byref(w))
+    if rc != BT_OK:
+        raise BitrussError(rc, "bt_estimate_bytes failed")
+    return int(b.value), int(w.value)
+
+
+def _torch_dtype(name):
+    try:
+        import torch
+    except ImportError:  # host-only use
+        return None
+    return {"uint64": getattr(torch, "uint64", torch.int64),
+            "uint32": getattr(torch, "uint32", torch.int32)}[name]

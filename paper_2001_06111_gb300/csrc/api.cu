@@ -1,0 +1,501 @@
+// C ABI of libbitruss (declared in include/bitruss.h): argument checks,
+// host/device staging, the handle's stream and memory pool, and the call
+// sequences CSR build -> wedge count -> BE-Index emit -> batch peel.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bt_internal.cuh"
+
+struct bt_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaMemPool_t pool = nullptr;
+    int num_sms = 0;
+    uint32_t *err_word = nullptr;  // device
+    bt::Index index;
+    bool has_index = false;
+    std::string err;
+    bt::Prof prof;
+    bt_profile last{};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(bt_handle *h, int code, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(bt_handle *h, cudaError_t e, const char *where) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(h, BT_ERR_NOMEM, "%s: device allocation failed (%s)", where, cudaGetErrorString(e));
+    return fail(h, BT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bt::Alloc make_alloc(bt_handle *h) {
+    bt::Alloc al;
+    al.stream = h->stream;
+    al.pool = h->pool;
+    al.prof = &h->prof;
+    return al;
+}
+
+// Starts a profiled call: clears the last profile and marks the call start.
+void call_begin(bt_handle *h, bt::Alloc &al, uint64_t m, uint32_t n) {
+    h->last = bt_profile{};
+    h->last.n_edges = m;
+    h->last.n_vertices = n;
+    for (bool &u : h->prof.used) u = false;
+    al.mark(bt::kPhTotal, false);
+}
+
+// Ends a profiled call: reads back the phase times.
+void call_end(bt_handle *h, bt::Alloc &al) {
+    al.mark(bt::kPhTotal, true);
+    h->last.launches = al.launches;
+    if (!h->prof.on) return;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return;
+    float *dst[bt::kNumPhases] = {&h->last.csr_ms, &h->last.count_ms, &h->last.emit_ms,
+                                  &h->last.peel_ms, &h->last.total_ms};
+    for (int p = 0; p < bt::kNumPhases; ++p) {
+        float ms = 0.f;
+        if (h->prof.used[p] &&
+            cudaEventElapsedTime(&ms, h->prof.ev[2 * p], h->prof.ev[2 * p + 1]) != cudaSuccess)
+            ms = 0.f;
+        *dst[p] = h->prof.used[p] ? ms : 0.f;
+    }
+}
+
+int check_args(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+               uint32_t flags) {
+    if (!h) return BT_ERR_ARG;
+    if (flags & ~(BT_DEVICE_PTRS | BT_TIE_LOWER_FIRST))
+        return fail(h, BT_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if (m > 0 && !edges) return fail(h, BT_ERR_ARG, "edges is NULL");
+    if ((uint64_t)nU + nL >= 0xFFFFFFFFull)
+        return fail(h, BT_ERR_ARG, "nU + nL = %llu exceeds 2^32 - 2",
+                    (unsigned long long)nU + nL);
+    if (m >= (1ull << 31)) return fail(h, BT_ERR_ARG, "m = %llu exceeds 2^31 - 1", (unsigned long long)m);
+    if (m > (uint64_t)nU * nL) return fail(h, BT_ERR_DUP, "m exceeds nU * nL: edges cannot be distinct");
+    return BT_OK;
+}
+
+// Stages the edge list on the device and builds the rank-ordered CSR.
+struct Prepared {
+    const int32_t *d_edges = nullptr;
+    int32_t *owned = nullptr;
+    bt::Csr g;
+};
+
+int prepare(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+            uint32_t flags, Prepared &P, bt::Alloc &al) {
+    if (flags & BT_DEVICE_PTRS) {
+        P.d_edges = edges;
+    } else {
+        P.owned = al.get<int32_t>(2 * m);
+        if (!P.owned) return cuda_fail(h, al.err, "staging edges");
+        cudaError_t e = cudaMemcpyAsync(P.owned, edges, sizeof(int32_t) * 2 * m,
+                                        cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copying edges to the device");
+        P.d_edges = P.owned;
+    }
+    cudaError_t e = cudaMemsetAsync(h->err_word, 0, sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = bt::build_csr(P.d_edges, m, nU, nL, flags, P.g, h->err_word, al);
+    if (e != cudaSuccess) return cuda_fail(h, e, "building the CSR");
+    uint32_t hw = 0;
+    e = cudaMemcpyAsync(&hw, h->err_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "building the CSR");
+    if (hw & bt::kErrRange) return fail(h, BT_ERR_RANGE, "a vertex id is outside [0,nU) x [0,nL)");
+    if (hw & bt::kErrDup) return fail(h, BT_ERR_DUP, "duplicate edge in the input");
+    return BT_OK;
+}
+
+void release(Prepared &P, bt::Alloc &al) {
+    bt::free_csr(P.g, al);
+    al.put(P.owned);
+    P.owned = nullptr;
+}
+
+// Copies a device result of `bytes` to the caller's buffer (host or device).
+cudaError_t deliver(bt_handle *h, void *dst, const void *src, size_t bytes, uint32_t flags) {
+    if (dst == src || bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes,
+                           (flags & BT_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           h->stream);
+}
+
+// Count (+ optional index).  d_support receives supports (device).
+int count_and_index(bt_handle *h, Prepared &P, uint64_t *d_support, bool want_index,
+                    bt::Index &ix, uint64_t &butterflies, bt::Alloc &al) {
+    bt::CountOut co;
+    co.support = d_support;
+    uint64_t W = 0;
+    if (want_index) {
+        co.inc_cnt = al.get<uint32_t>(P.g.m);
+        co.w2v = al.get<uint64_t>(P.g.n);
+        co.nbv = al.get<uint64_t>(P.g.n);
+        if (al.err != cudaSuccess) return cuda_fail(h, al.err, "allocating count buffers");
+    }
+    cudaError_t e = bt::count_wedges(P.g, co, h->num_sms, al);
+    if (e != cudaSuccess) return cuda_fail(h, e, "counting wedges");
+    unsigned long long bf = 0;
+    e = cudaMemcpyAsync(&bf, co.butterflies_dev, sizeof(bf), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    al.put(co.butterflies_dev);
+    if (e != cudaSuccess) return cuda_fail(h, e, "counting wedges");
+    butterflies = bf;
+    if (want_index) {
+        // W for the statistics: sum of wedges per start vertex
+        uint64_t *tot = al.get<uint64_t>(1);
+        uint64_t *scratch = al.get<uint64_t>(P.g.n);
+        if (al.err != cudaSuccess) return cuda_fail(h, al.err, "allocating");
+        e = bt::exclusive_scan_u64(P.g.wv, scratch, P.g.n, tot, al);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&W, tot, sizeof(W), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        al.put(tot);
+        al.put(scratch);
+        if (e != cudaSuccess) return cuda_fail(h, e, "summing wedges");
+        e = bt::emit_index(P.g, co, ix, h->num_sms, al, h->stream);
+        al.put(co.inc_cnt);
+        al.put(co.w2v);
+        al.put(co.nbv);
+        if (e == cudaErrorInvalidValue)
+            return fail(h, BT_ERR_OVERFLOW, "BE-Index has >= 2^32 twin pairs or blooms");
+        if (e != cudaSuccess) return cuda_fail(h, e, "emitting the BE-Index");
+        ix.w = W;
+        ix.butterflies = bf;
+    }
+    return BT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bt_create(bt_handle **out, int device, void *cuda_stream) {
+    if (!out) return BT_ERR_ARG;
+    *out = nullptr;
+    bt_handle *h = new (std::nothrow) bt_handle();
+    if (!h) return BT_ERR_NOMEM;
+    h->device = device;
+    DeviceGuard dg(device);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) {
+            h->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            h->own_stream = true;
+        }
+    }
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&h->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        uint64_t thr = ~0ull;  // keep freed blocks cached for the next call
+        e = cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&h->err_word, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        if (h->pool) cudaMemPoolDestroy(h->pool);
+        delete h;
+        return e == cudaErrorMemoryAllocation ? BT_ERR_NOMEM : BT_ERR_CUDA;
+    }
+    *out = h;
+    return BT_OK;
+}
+
+int bt_destroy(bt_handle *h) {
+    if (!h) return BT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    if (h->has_index) {
+        bt::Alloc al = make_alloc(h);
+        bt::free_index(h->index, al);
+    }
+    cudaStreamSynchronize(h->stream);
+    for (auto &ev : h->prof.ev)
+        if (ev) cudaEventDestroy(ev);
+    cudaFree(h->err_word);
+    if (h->pool) cudaMemPoolDestroy(h->pool);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return BT_OK;
+}
+
+const char *bt_last_error(const bt_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int bt_count_support(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                     uint64_t *support_out, uint32_t flags) {
+    int rc = check_args(h, edges, m, nU, nL, flags);
+    if (rc) return rc;
+    h->err.clear();
+    if (m == 0) return BT_OK;
+    if (!support_out) return fail(h, BT_ERR_ARG, "support_out is NULL");
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    call_begin(h, al, m, nU + nL);
+    Prepared P;
+    rc = prepare(h, edges, m, nU, nL, flags, P, al);
+    uint64_t *d_sup = nullptr;
+    if (rc == BT_OK) {
+        d_sup = (flags & BT_DEVICE_PTRS) ? support_out : al.get<uint64_t>(m);
+        if (!d_sup) rc = cuda_fail(h, al.err, "allocating supports");
+    }
+    bt::Index unused;
+    uint64_t bf = 0;
+    if (rc == BT_OK) rc = count_and_index(h, P, d_sup, false, unused, bf, al);
+    if (rc == BT_OK) {
+        cudaError_t e = deliver(h, support_out, d_sup, sizeof(uint64_t) * m, flags);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "returning supports");
+    }
+    if (!(flags & BT_DEVICE_PTRS)) al.put(d_sup);
+    release(P, al);
+    call_end(h, al);
+    cudaStreamSynchronize(h->stream);
+    return rc;
+}
+
+static int build_index_impl(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU,
+                            uint32_t nL, uint32_t flags, uint64_t *d_sup, bt::Alloc &al) {
+    Prepared P;
+    int rc = prepare(h, edges, m, nU, nL, flags, P, al);
+    if (h->has_index) {
+        bt::free_index(h->index, al);
+        h->has_index = false;
+    }
+    bt::Index ix;
+    uint64_t bf = 0;
+    if (rc == BT_OK) rc = count_and_index(h, P, d_sup, true, ix, bf, al);
+    release(P, al);
+    if (rc == BT_OK) {
+        h->index = ix;
+        h->has_index = true;
+    } else {
+        bt::free_index(ix, al);
+    }
+    return rc;
+}
+
+int bt_build_index(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                   bt_index_stats *stats_out, uint32_t flags) {
+    int rc = check_args(h, edges, m, nU, nL, flags);
+    if (rc) return rc;
+    h->err.clear();
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    call_begin(h, al, m, nU + nL);
+    uint64_t *d_sup = al.get<uint64_t>(m);
+    if (!d_sup) return cuda_fail(h, al.err, "allocating supports");
+    if (m == 0) {
+        if (h->has_index) bt::free_index(h->index, al);
+        h->index = bt::Index{};
+        h->has_index = true;
+        rc = BT_OK;
+    } else {
+        rc = build_index_impl(h, edges, m, nU, nL, flags, d_sup, al);
+    }
+    al.put(d_sup);
+    call_end(h, al);
+    if (rc == BT_OK) {
+        h->last.n_wedges = h->index.w;
+        h->last.n_bloom_wedges = h->index.w2;
+        h->last.n_blooms = h->index.nb;
+    }
+    cudaStreamSynchronize(h->stream);
+    if (rc == BT_OK && stats_out) {
+        stats_out->n_wedges = h->index.w;
+        stats_out->n_bloom_wedges = h->index.w2;
+        stats_out->n_blooms = h->index.nb;
+        stats_out->n_butterflies = h->index.butterflies;
+        stats_out->index_bytes = h->index.bytes();
+    }
+    return rc;
+}
+
+int bt_index_export(bt_handle *h, bt_bloom_rec *blooms_out, uint32_t *pairs_out,
+                    uint32_t *edge_deg_out) {
+    if (!h) return BT_ERR_ARG;
+    if (!h->has_index) return fail(h, BT_ERR_STATE, "no BE-Index has been built on this handle");
+    DeviceGuard dg(h->device);
+    const bt::Index &ix = h->index;
+    cudaError_t e = cudaSuccess;
+    if (blooms_out && ix.nb) {
+        std::vector<uint32_t> k(ix.nb), off(ix.nb);
+        e = cudaMemcpyAsync(k.data(), ix.bloom_k, 4 * ix.nb, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(off.data(), ix.bloom_off, 4 * ix.nb, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess)
+            for (uint64_t i = 0; i < ix.nb; ++i) blooms_out[i] = bt_bloom_rec{k[i], off[i]};
+    }
+    if (e == cudaSuccess && pairs_out && ix.w2)
+        e = cudaMemcpyAsync(pairs_out, ix.pairs, 8 * ix.w2, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && edge_deg_out && ix.m) {
+        std::vector<uint64_t> off(ix.m + 1);
+        e = cudaMemcpyAsync(off.data(), ix.inc_off, 8 * (ix.m + 1), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess)
+            for (uint64_t i = 0; i < ix.m; ++i) edge_deg_out[i] = (uint32_t)(off[i + 1] - off[i]);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "exporting the index");
+    return BT_OK;
+}
+
+int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                 uint64_t *support_out, uint32_t *phi_out, bt_peel_stats *stats, uint32_t flags) {
+    int rc = check_args(h, edges, m, nU, nL, flags);
+    if (rc) return rc;
+    h->err.clear();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (m == 0) return BT_OK;
+    if (!phi_out) return fail(h, BT_ERR_ARG, "phi_out is NULL");
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    call_begin(h, al, m, nU + nL);
+    const bool dev = flags & BT_DEVICE_PTRS;
+    uint64_t *d_sup = (dev && support_out) ? support_out : al.get<uint64_t>(m);
+    uint32_t *d_phi = dev ? phi_out : al.get<uint32_t>(m);
+    if (al.err != cudaSuccess) return cuda_fail(h, al.err, "allocating outputs");
+    rc = build_index_impl(h, edges, m, nU, nL, flags, d_sup, al);
+    bt::PeelResult pr;
+    if (rc == BT_OK) {
+        cudaError_t e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
+        else if (pr.status == BT_ERR_OVERFLOW)
+            rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
+        else if (pr.status != BT_OK)
+            rc = fail(h, pr.status, "peeling did not converge within its round limit");
+    }
+    if (rc == BT_OK) {
+        cudaError_t e = cudaSuccess;
+        if (support_out) e = deliver(h, support_out, d_sup, sizeof(uint64_t) * m, flags);
+        if (e == cudaSuccess) e = deliver(h, phi_out, d_phi, sizeof(uint32_t) * m, flags);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "returning results");
+    }
+    if (stats && rc == BT_OK) {
+        stats->rounds = pr.rounds;
+        stats->levels = pr.levels;
+        stats->support_updates = pr.updates;
+        stats->phi_max = (uint32_t)pr.kmax;
+    }
+    if (!(dev && support_out)) al.put(d_sup);
+    if (!dev) al.put(d_phi);
+    call_end(h, al);
+    if (rc == BT_OK) {
+        h->last.n_wedges = h->index.w;
+        h->last.n_bloom_wedges = h->index.w2;
+        h->last.n_blooms = h->index.nb;
+        h->last.rounds = pr.rounds;
+        h->last.levels = pr.levels;
+        h->last.support_updates = pr.updates;
+    }
+    cudaStreamSynchronize(h->stream);
+    return rc;
+}
+
+int bt_profile_enable(bt_handle *h, int on) {
+    if (!h) return BT_ERR_ARG;
+    DeviceGuard dg(h->device);
+    if (on && !h->prof.ev[0]) {
+        for (auto &ev : h->prof.ev) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return cuda_fail(h, e, "creating profiling events");
+        }
+    }
+    h->prof.on = on != 0;
+    return BT_OK;
+}
+
+int bt_profile_read(const bt_handle *h, bt_profile *out) {
+    if (!h || !out) return BT_ERR_ARG;
+    *out = h->last;
+    return BT_OK;
+}
+
+int bt_estimate_bytes(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
+                      uint64_t *bytes_out, uint64_t *wedges_out) {
+    if (!bytes_out || (m && !edges)) return BT_ERR_ARG;
+    if ((uint64_t)nU + nL >= 0xFFFFFFFFull || m >= (1ull << 31)) return BT_ERR_ARG;
+    const uint64_t n = (uint64_t)nU + nL;
+    std::vector<uint32_t> deg(n, 0);
+    auto gid_u = [&](uint32_t u) { return (flags & BT_TIE_LOWER_FIRST) ? u : nL + u; };
+    auto gid_v = [&](uint32_t v) { return (flags & BT_TIE_LOWER_FIRST) ? nU + v : v; };
+    for (uint64_t i = 0; i < m; ++i) {
+        int32_t u = edges[2 * i], v = edges[2 * i + 1];
+        if (u < 0 || v < 0 || (uint32_t)u >= nU || (uint32_t)v >= nL) return BT_ERR_RANGE;
+        deg[gid_u(u)]++;
+        deg[gid_v(v)]++;
+    }
+    // rank by (degree, id)
+    std::vector<uint32_t> order(n), rank(n);
+    for (uint64_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return deg[a] < deg[b]; });
+    for (uint64_t r = 0; r < n; ++r) rank[order[r]] = (uint32_t)r;
+    std::vector<uint64_t> off(n + 1, 0);
+    for (uint64_t x = 0; x < n; ++x) off[rank[x] + 1] = deg[x];
+    for (uint64_t r = 0; r < n; ++r) off[r + 1] += off[r];
+    std::vector<uint32_t> adj(2 * m);
+    std::vector<uint64_t> fill(off.begin(), off.end() - 1);
+    for (uint64_t i = 0; i < m; ++i) {
+        uint32_t a = rank[gid_u(edges[2 * i])], b = rank[gid_v(edges[2 * i + 1])];
+        adj[fill[a]++] = b;
+        adj[fill[b]++] = a;
+    }
+    for (uint64_t r = 0; r < n; ++r) std::sort(adj.begin() + off[r], adj.begin() + off[r + 1]);
+    uint64_t W = 0;
+    for (uint64_t u = 0; u < n; ++u)
+        for (uint64_t j = off[u]; j < off[u + 1]; ++j) {
+            uint32_t v = adj[j];
+            if (v >= u) break;
+            W += (uint64_t)(std::lower_bound(adj.begin() + off[v], adj.begin() + off[v + 1], (uint32_t)u) -
+                            (adj.begin() + off[v]));
+        }
+    if (wedges_out) *wedges_out = W;
+    // CSR + sort scratch + counters (peak), supports/phi/peel state, and an
+    // index bound of 16 bytes per wedge plus per-bloom records (<= W/2 blooms)
+    uint64_t csr = (n + 1) * 8 + 2 * m * (4 + 4 + 4) + n * 12;
+    uint64_t sort_scratch = 2 * m * 24;
+    uint64_t counters = 2ull * 152 * 2 * n * 4;
+    uint64_t edges_b = m * (8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4);
+    uint64_t index_b = W * (8 + 4 + 8 + 1) + (W / 2 + 1) * 16;
+    *bytes_out = csr + std::max(sort_scratch, counters) + edges_b + index_b + (1ull << 20);
+    return BT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal declarations shared by the CUDA translation units of libbitruss.
+// Nothing here is part of the public ABI (include/bitruss.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/bitruss.h"
+
+namespace bt {
+
+constexpr uint32_t kAlive = 0xFFFFFFFFu;  // edge state: unassigned, not queued
+
+// Device error word bits (written with atomicOr, read back by the host).
+enum : uint32_t {
+    kErrRange = 1u << 0,
+    kErrDup = 1u << 1,
+    kErrOverflow = 1u << 2,
+};
+
+// Optional per-phase CUDA-event timing (bt_profile_enable).
+enum Phase { kPhCsr = 0, kPhCount = 1, kPhEmit = 2, kPhPeel = 3, kPhTotal = 4, kNumPhases = 5 };
+struct Prof {
+    bool on = false;
+    cudaEvent_t ev[2 * kNumPhases] = {};
+    bool used[kNumPhases] = {};
+};
+
+// Stream-ordered scratch allocation from the handle's memory pool, plus the
+// call's launch counter and profiler.
+struct Alloc {
+    cudaStream_t stream;
+    cudaMemPool_t pool;
+    cudaError_t err = cudaSuccess;
+    uint64_t launches = 0;
+    Prof *prof = nullptr;
+    void mark(int phase, bool end) {
+        if (prof && prof->on) {
+            cudaEventRecord(prof->ev[2 * phase + (end ? 1 : 0)], stream);
+            prof->used[phase] = true;
+        }
+    }
+    template <typename T>
+    T *get(size_t count) {
+        if (err != cudaSuccess) return nullptr;
+        void *p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        err = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
+        return err == cudaSuccess ? static_cast<T *>(p) : nullptr;
+    }
+    void put(void *p) {
+        if (p) cudaFreeAsync(p, stream);
+    }
+};
+
+// ---------------------------------------------------------------- scan/sort
+// Exclusive prefix sum of n values (in-place allowed).  Writes the grand total
+// to *total (device pointer) when total != nullptr.
+cudaError_t exclusive_scan_u32(const uint32_t *in, uint32_t *out, size_t n, uint32_t *total,
+                               Alloc &al);
+cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, size_t n, uint64_t *total,
+                               Alloc &al);
+// out[i] = in[i] widened to 64 bits.
+cudaError_t widen_u32(const uint32_t *in, uint64_t *out, size_t n, Alloc &al);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys.  Result ends in (keys, vals); (tk, tv) are scratch of the same size.
+cudaError_t radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *tk, uint32_t *tv, size_t n,
+                           int bits, Alloc &al);
+cudaError_t radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *tk, uint32_t *tv, size_t n,
+                           int bits, Alloc &al);
+
+// ---------------------------------------------------------------- graph
+// Rank-ordered CSR over one id space of n = nU + nL vertices.  Vertex r is
+// the vertex of rank r (priority order of Def. 7: degree, then global id);
+// adjacency lists hold neighbour ranks sorted ascending, eid the edge ids.
+struct Csr {
+    uint32_t n = 0;
+    uint64_t m = 0;
+    uint64_t *off = nullptr;  // [n+1]
+    uint32_t *adj = nullptr;  // [2m]
+    uint32_t *eid = nullptr;  // [2m]
+    uint32_t *hv = nullptr;   // [n] #neighbours of lower rank (a prefix of the list)
+    uint32_t *pl = nullptr;   // [2m] for arc (u->v), v<u: #w in N(v) with w<u; else 0
+    uint64_t *wv = nullptr;   // [n] priority-obeyed wedges started at each vertex
+};
+
+// Builds the CSR (and wedge prefix lengths) from a device edge list.
+// err_word: device u32 receiving kErr* bits.  Returns a CUDA error.
+cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
+                      Csr &g, uint32_t *err_word, Alloc &al);
+void free_csr(Csr &g, Alloc &al);
+
+// ---------------------------------------------------------------- counting
+struct CountOut {
+    uint64_t *support = nullptr;  // [m] (caller-provided, zeroed by count)
+    uint32_t *inc_cnt = nullptr;  // [m] links per edge (index mode) or nullptr
+    uint64_t *w2v = nullptr;      // [n] bloom wedges per start vertex (index mode)
+    uint64_t *nbv = nullptr;      // [n] blooms per start vertex (index mode)
+    unsigned long long *butterflies_dev = nullptr;  // [1] set by count_wedges; caller frees
+};
+cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al);
+
+// Device-resident BE-Index (Section IV-A).
+struct Index {
+    uint64_t m = 0;
+    uint64_t nb = 0;             // blooms
+    uint64_t w2 = 0;             // twin pairs (= links / 2)
+    uint64_t w = 0;              // priority-obeyed wedges
+    uint64_t butterflies = 0;
+    uint32_t *bloom_k = nullptr;     // [nb] bloom numbers
+    uint32_t *bloom_off = nullptr;   // [nb+1] first pair of each bloom
+    uint2 *pairs = nullptr;          // [w2] (e_uv, e_vw) twin edge ids
+    uint32_t *pair_bloom = nullptr;  // [w2]
+    uint64_t *inc_off = nullptr;     // [m+1]
+    uint32_t *inc = nullptr;         // [2*w2] pair ids linked to each edge
+    size_t bytes() const {
+        return nb * 8 + 4 + w2 * 12 + (m + 1) * 8 + w2 * 8;
+    }
+};
+cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, Alloc &al,
+                       cudaStream_t stream);
+void free_index(Index &ix, Alloc &al);
+
+// ---------------------------------------------------------------- peeling
+struct PeelResult {
+    uint64_t rounds = 0, levels = 0, updates = 0, kmax = 0;
+    int status = BT_OK;
+};
+// support: [m] initial supports (device, preserved); phi_out: [m] device.
+cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
+                 int num_sms, Alloc &al);
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline int bits_for(uint64_t maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+}  // namespace bt
+
+#define BT_CUDA(x)                          \
+    do {                                    \
+        cudaError_t e_ = (x);               \
+        if (e_ != cudaSuccess) return e_;   \
+    } while (0)

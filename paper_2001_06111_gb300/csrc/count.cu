@@ -1,0 +1,381 @@
+// Butterfly support counting and BE-Index construction by priority-obeyed
+// wedge enumeration (Section IV-B, Alg. 3; Defs. 7, 8, 10).
+//
+// For a start vertex u (processed in rank space, so p(x) < p(u) <=> x < u):
+//   pass A  for v in N(u), v < u; for w in N(v), w < u:  cnt[w] += 1
+//           -> cnt[w] = |N(u) ∩ N(w) ∩ {x < u}|  (Alg. 3, the first wedge loop)
+//   pass B  every wedge (u,v,w) with c = cnt[w] >= 2 lies in the maximal
+//           priority-obeyed bloom anchored by (u,w), a c-bloom (Lemma 7); each
+//           of its two edges is in c-1 of the bloom's butterflies (Lemma 2)
+//           and every butterfly lies in exactly one such bloom (Lemma 3), so
+//           support(u,v) += c-1 and support(v,w) += c-1 sums to the support.
+//   emit    the bloom gets bloom number c, and the wedge becomes one twin
+//           pair ((u,v),(v,w)) linked to it (Alg. 3, the second wedge loop).
+//
+// Work layout: persistent blocks pull start vertices from a global queue in
+// decreasing rank (heaviest first).  A block enumerates the wedges of its
+// vertex in chunks of kThreads middle vertices: a block scan of the per-arc
+// prefix lengths flattens the chunk's wedges, so every thread handles whole
+// wedges regardless of the degree skew.  Counters are a dense per-block
+// array indexed by rank, kept at zero between vertices (it is reset by the
+// same wedge walk that filled it).
+#include "bt_device.cuh"
+#include "bt_internal.cuh"
+
+namespace bt {
+namespace {
+
+constexpr int kThreads = 512;
+
+struct Chunk {
+    uint32_t off[kThreads + 1];  // exclusive prefix of wedge counts; off[kThreads] = total
+    uint32_t v[kThreads];        // middle vertex (rank)
+    uint32_t e[kThreads];        // edge id of (u, v)
+};
+
+// Loads middle vertices [c0, c0 + kThreads) of start vertex u.  Returns the
+// number of wedges in the chunk.  Contains __syncthreads().
+__device__ __forceinline__ uint32_t load_chunk(Chunk &ch, const uint32_t *adj, const uint32_t *eid,
+                                               const uint32_t *pl, uint64_t a, uint32_t h,
+                                               uint32_t c0) {
+    uint32_t i = c0 + threadIdx.x;
+    uint32_t p = 0, v = 0, e = 0;
+    if (i < h) {
+        p = pl[a + i];
+        v = adj[a + i];
+        e = eid[a + i];
+    }
+    uint32_t tot;
+    uint32_t ex = dev::block_excl_scan<uint32_t>(p, &tot);
+    ch.off[threadIdx.x] = ex;
+    ch.v[threadIdx.x] = v;
+    ch.e[threadIdx.x] = e;
+    if (threadIdx.x == 0) ch.off[kThreads] = tot;
+    __syncthreads();
+    return tot;
+}
+
+// Wedge t of the chunk -> (chunk slot vi, arc index of (v, w) in the CSR).
+__device__ __forceinline__ uint64_t wedge_arc(const Chunk &ch, const uint64_t *off, uint32_t t,
+                                              uint32_t &vi) {
+    vi = dev::last_le_u32(ch.off, kThreads, t);
+    return off[ch.v[vi]] + (t - ch.off[vi]);
+}
+
+__device__ __forceinline__ uint32_t next_vertex(uint32_t *queue, uint32_t n, uint32_t *s_q) {
+    if (threadIdx.x == 0) *s_q = atomicAdd(queue, 1u);
+    __syncthreads();
+    uint32_t qi = *s_q;
+    __syncthreads();
+    return qi < n ? n - 1 - qi : 0xFFFFFFFFu;
+}
+
+__device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
+
+// Pass A over all chunks of u.
+__device__ void pass_count(Chunk &ch, const uint64_t *off, const uint32_t *adj,
+                           const uint32_t *eid, const uint32_t *pl, uint64_t a, uint32_t h,
+                           uint32_t *cnt) {
+    for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+        uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
+        for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+            uint32_t vi;
+            uint64_t arc = wedge_arc(ch, off, t, vi);
+            atomicAdd(&cnt[adj[arc]], 1u);
+        }
+        __syncthreads();
+    }
+}
+
+template <bool kIndex>
+__global__ void __launch_bounds__(kThreads) k_count(
+    const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
+    const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
+    const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
+    uint32_t *cnt_all, unsigned long long *support, uint32_t *inc_cnt, uint64_t *w2v,
+    uint64_t *nbv, unsigned long long *totals, uint32_t *queue) {
+    __shared__ Chunk ch;
+    __shared__ unsigned long long s_acc[kThreads];
+    __shared__ uint32_t s_inc[kThreads];
+    __shared__ uint32_t s_q;
+    uint32_t *cnt = cnt_all + (size_t)blockIdx.x * n;
+    s_acc[threadIdx.x] = 0;
+    s_inc[threadIdx.x] = 0;
+    unsigned long long bf_total = 0;
+    for (;;) {
+        uint32_t u = next_vertex(queue, n, &s_q);
+        if (u == 0xFFFFFFFFu) break;
+        if (wv[u] == 0) {
+            if (kIndex && threadIdx.x == 0) {
+                w2v[u] = 0;
+                nbv[u] = 0;
+            }
+            continue;
+        }
+        const uint64_t a = off[u];
+        const uint32_t h = hv[u];
+        pass_count(ch, off, adj, eid, pl, a, h, cnt);
+        // pass B: attribute c-1 to both edges of every wedge in a bloom
+        unsigned long long w2_local = 0;
+        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+            uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
+            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+                uint32_t vi;
+                uint64_t arc = wedge_arc(ch, off, t, vi);
+                uint32_t c = ld_cg(&cnt[adj[arc]]);
+                if (c >= 2) {
+                    uint32_t evw = eid[arc];
+                    atomicAdd(&support[evw], (unsigned long long)(c - 1));
+                    atomicAdd(&s_acc[vi], (unsigned long long)(c - 1));
+                    if (kIndex) {
+                        atomicAdd(&inc_cnt[evw], 1u);
+                        atomicAdd(&s_inc[vi], 1u);
+                        ++w2_local;
+                    }
+                }
+            }
+            __syncthreads();
+            if (s_acc[threadIdx.x]) {
+                atomicAdd(&support[ch.e[threadIdx.x]], s_acc[threadIdx.x]);
+                s_acc[threadIdx.x] = 0;
+            }
+            if (kIndex && s_inc[threadIdx.x]) {
+                atomicAdd(&inc_cnt[ch.e[threadIdx.x]], s_inc[threadIdx.x]);
+                s_inc[threadIdx.x] = 0;
+            }
+            __syncthreads();
+        }
+        // pass C: reset counters; the first thread to clear a bloom counts it
+        unsigned long long nb_local = 0;
+        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+            uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
+            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+                uint32_t vi;
+                uint64_t arc = wedge_arc(ch, off, t, vi);
+                uint32_t old = atomicExch(&cnt[adj[arc]], 0u);
+                if (old >= 2) {
+                    ++nb_local;
+                    bf_total += (unsigned long long)old * (old - 1) / 2;
+                }
+            }
+            __syncthreads();
+        }
+        if (kIndex) {
+            unsigned long long w2s = dev::block_sum(w2_local);
+            unsigned long long nbs = dev::block_sum(nb_local);
+            if (threadIdx.x == 0) {
+                w2v[u] = w2s;
+                nbv[u] = nbs;
+            }
+        }
+    }
+    bf_total = dev::block_sum(bf_total);
+    if (threadIdx.x == 0 && bf_total) atomicAdd(&totals[0], bf_total);
+}
+
+// Emit the index: blooms (bloom number, first pair), twin pairs and the
+// per-edge link lists.  aux_all is a second dense per-block array.
+__global__ void __launch_bounds__(kThreads) k_emit(
+    const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
+    const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
+    const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
+    uint32_t *cnt_all, uint32_t *aux_all, const uint64_t *__restrict__ bloom_base,
+    const uint64_t *__restrict__ pair_base, const uint64_t *__restrict__ inc_off,
+    uint32_t *inc_fill, uint32_t *bloom_k, uint32_t *bloom_off, uint2 *pairs,
+    uint32_t *pair_bloom, uint32_t *inc, uint32_t *queue) {
+    __shared__ Chunk ch;
+    __shared__ uint32_t s_q;
+    __shared__ uint32_t s_nb, s_np;
+    uint32_t *cnt = cnt_all + (size_t)blockIdx.x * n;
+    uint32_t *aux = aux_all + (size_t)blockIdx.x * n;
+    for (;;) {
+        uint32_t u = next_vertex(queue, n, &s_q);
+        if (u == 0xFFFFFFFFu) break;
+        if (wv[u] == 0) continue;
+        const uint64_t a = off[u];
+        const uint32_t h = hv[u];
+        const uint64_t bb = bloom_base[u];
+        const uint64_t pb = pair_base[u];
+        if (threadIdx.x == 0) {
+            s_nb = 0;
+            s_np = 0;
+        }
+        pass_count(ch, off, adj, eid, pl, a, h, cnt);
+        // claim: one thread per bloom allocates its id and pair range
+        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+            uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
+            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+                uint32_t vi;
+                uint64_t arc = wedge_arc(ch, off, t, vi);
+                uint32_t w = adj[arc];
+                uint32_t c = ld_cg(&cnt[w]);
+                if (c >= 2 && atomicCAS(&aux[w], 0u, 1u) == 0u) {
+                    uint32_t j = atomicAdd(&s_nb, 1u);
+                    uint32_t p = atomicAdd(&s_np, c);
+                    uint64_t B = bb + j;
+                    bloom_k[B] = c;
+                    bloom_off[B] = (uint32_t)(pb + p);
+                    atomicExch(&aux[w], j + 2u);
+                }
+            }
+            __syncthreads();
+        }
+        // place each bloom wedge as a twin pair and link both edges to it
+        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+            uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
+            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+                uint32_t vi;
+                uint64_t arc = wedge_arc(ch, off, t, vi);
+                uint32_t w = adj[arc];
+                uint32_t x = ld_cg(&aux[w]);
+                if (x >= 2) {
+                    uint64_t B = bb + (x - 2);
+                    uint32_t pos = atomicSub(&cnt[w], 1u) - 1u;
+                    uint32_t slot = ld_cg(&bloom_off[B]) + pos;
+                    uint32_t euv = ch.e[vi], evw = eid[arc];
+                    pairs[slot] = make_uint2(euv, evw);
+                    pair_bloom[slot] = (uint32_t)B;
+                    uint32_t q1 = atomicAdd(&inc_fill[euv], 1u);
+                    inc[inc_off[euv] + q1] = slot;
+                    uint32_t q2 = atomicAdd(&inc_fill[evw], 1u);
+                    inc[inc_off[evw] + q2] = slot;
+                }
+            }
+            __syncthreads();
+        }
+        // reset: blooms already drained cnt to zero; clear aux and single wedges
+        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+            uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
+            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+                uint32_t vi;
+                uint64_t arc = wedge_arc(ch, off, t, vi);
+                uint32_t w = adj[arc];
+                if (ld_cg(&aux[w]) == 0u) cnt[w] = 0u;
+                else aux[w] = 0u;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+int blocks_per_sm_count() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_count<true>, kThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+}  // namespace
+
+cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al) {
+    const bool index = o.inc_cnt != nullptr;
+    const uint32_t n = g.n;
+    int bps = blocks_per_sm_count();
+    unsigned blocks = (unsigned)(num_sms * bps);
+    uint32_t *cnt = al.get<uint32_t>((size_t)blocks * n);
+    uint32_t *queue = al.get<uint32_t>(1);
+    unsigned long long *totals = al.get<unsigned long long>(1);
+    if (al.err != cudaSuccess) return al.err;
+    BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)blocks * n, al.stream));
+    BT_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), al.stream));
+    BT_CUDA(cudaMemsetAsync(totals, 0, sizeof(unsigned long long), al.stream));
+    BT_CUDA(cudaMemsetAsync(o.support, 0, sizeof(uint64_t) * g.m, al.stream));
+    if (index) BT_CUDA(cudaMemsetAsync(o.inc_cnt, 0, sizeof(uint32_t) * g.m, al.stream));
+    auto *sup = reinterpret_cast<unsigned long long *>(o.support);
+    al.mark(kPhCount, false);
+    if (index) {
+        k_count<true><<<blocks, kThreads, 0, al.stream>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n,
+                                                          cnt, sup, o.inc_cnt, o.w2v, o.nbv,
+                                                          totals, queue);
+    } else {
+        k_count<false><<<blocks, kThreads, 0, al.stream>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n,
+                                                           cnt, sup, nullptr, nullptr, nullptr,
+                                                           totals, queue);
+    }
+    al.launches++;
+    al.mark(kPhCount, true);
+    BT_CUDA(cudaGetLastError());
+    o.butterflies_dev = totals;
+    al.put(cnt);
+    al.put(queue);
+    return cudaSuccess;
+}
+
+cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, Alloc &al,
+                       cudaStream_t stream) {
+    const uint32_t n = g.n;
+    const uint64_t m = g.m;
+    ix.m = m;
+    // layout prefix sums
+    uint64_t *bloom_base = al.get<uint64_t>(n);
+    uint64_t *pair_base = al.get<uint64_t>(n);
+    uint64_t *tot = al.get<uint64_t>(3);
+    uint64_t *incc64 = al.get<uint64_t>(m + 1);
+    ix.inc_off = al.get<uint64_t>(m + 1);
+    if (al.err != cudaSuccess) return al.err;
+    BT_CUDA(exclusive_scan_u64(c.nbv, bloom_base, n, tot + 0, al));
+    BT_CUDA(exclusive_scan_u64(c.w2v, pair_base, n, tot + 1, al));
+    BT_CUDA(widen_u32(c.inc_cnt, incc64, m, al));
+    BT_CUDA(cudaMemsetAsync(incc64 + m, 0, sizeof(uint64_t), al.stream));
+    BT_CUDA(exclusive_scan_u64(incc64, ix.inc_off, m + 1, nullptr, al));
+    al.put(incc64);
+    uint64_t h_tot[2];
+    BT_CUDA(cudaMemcpyAsync(h_tot, tot, sizeof(h_tot), cudaMemcpyDeviceToHost, stream));
+    BT_CUDA(cudaStreamSynchronize(stream));
+    ix.nb = h_tot[0];
+    ix.w2 = h_tot[1];
+    if (ix.w2 >= 0xFFFFFFFFull || ix.nb >= 0xFFFFFFFFull) {
+        al.put(bloom_base);
+        al.put(pair_base);
+        al.put(tot);
+        return cudaErrorInvalidValue;  // reported as overflow by the caller
+    }
+    ix.bloom_k = al.get<uint32_t>(ix.nb);
+    ix.bloom_off = al.get<uint32_t>(ix.nb + 1);
+    ix.pairs = al.get<uint2>(ix.w2);
+    ix.pair_bloom = al.get<uint32_t>(ix.w2);
+    ix.inc = al.get<uint32_t>(2 * ix.w2);
+    uint32_t *inc_fill = al.get<uint32_t>(m);
+    int bps = blocks_per_sm_count();
+    unsigned blocks = (unsigned)(num_sms * bps);
+    uint32_t *cnt = al.get<uint32_t>((size_t)blocks * n);
+    uint32_t *aux = al.get<uint32_t>((size_t)blocks * n);
+    uint32_t *queue = al.get<uint32_t>(1);
+    if (al.err != cudaSuccess) return al.err;
+    uint32_t w2_32 = (uint32_t)ix.w2;
+    BT_CUDA(cudaMemcpyAsync(ix.bloom_off + ix.nb, &w2_32, sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            stream));
+    BT_CUDA(cudaMemsetAsync(inc_fill, 0, sizeof(uint32_t) * m, al.stream));
+    BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)blocks * n, al.stream));
+    BT_CUDA(cudaMemsetAsync(aux, 0, sizeof(uint32_t) * (size_t)blocks * n, al.stream));
+    BT_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), al.stream));
+    al.mark(kPhEmit, false);
+    k_emit<<<blocks, kThreads, 0, al.stream>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, cnt, aux,
+                                               bloom_base, pair_base, ix.inc_off, inc_fill,
+                                               ix.bloom_k, ix.bloom_off, ix.pairs, ix.pair_bloom,
+                                               ix.inc, queue);
+    al.launches++;
+    al.mark(kPhEmit, true);
+    BT_CUDA(cudaGetLastError());
+    // the host copy of w2_32 must outlive the async copy
+    BT_CUDA(cudaStreamSynchronize(stream));
+    al.put(cnt);
+    al.put(aux);
+    al.put(queue);
+    al.put(inc_fill);
+    al.put(bloom_base);
+    al.put(pair_base);
+    al.put(tot);
+    return cudaSuccess;
+}
+
+void free_index(Index &ix, Alloc &al) {
+    al.put(ix.bloom_k);
+    al.put(ix.bloom_off);
+    al.put(ix.pairs);
+    al.put(ix.pair_bloom);
+    al.put(ix.inc_off);
+    al.put(ix.inc);
+    ix = Index{};
+}
+
+}  // namespace bt

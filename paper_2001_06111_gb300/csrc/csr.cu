@@ -1,0 +1,205 @@
+// Degree, priority rank and rank-ordered CSR (the preprocessing of Alg. 3:
+// "compute p(u) for each u", Def. 7), plus the per-arc wedge prefix lengths
+// that bound the priority-obeyed wedge loops (Def. 10, Lemma 6).
+#include "bt_internal.cuh"
+
+namespace bt {
+namespace {
+
+// Global id of each endpoint.  Section II assumes every upper id exceeds
+// every lower id: lower v -> v, upper u -> nL + u.  BT_TIE_LOWER_FIRST swaps
+// the layers (upper u -> u, lower v -> nU + v).
+__device__ __forceinline__ void gids(int32_t u, int32_t v, uint32_t nU, uint32_t nL, uint32_t flags,
+                                     uint32_t &gu, uint32_t &gv) {
+    if (flags & BT_TIE_LOWER_FIRST) {
+        gu = (uint32_t)u;
+        gv = nU + (uint32_t)v;
+    } else {
+        gu = nL + (uint32_t)u;
+        gv = (uint32_t)v;
+    }
+}
+
+__global__ void k_degree(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
+                         uint32_t *deg, uint32_t *err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        int2 e = reinterpret_cast<const int2 *>(edges)[i];
+        if (e.x < 0 || e.y < 0 || (uint32_t)e.x >= nU || (uint32_t)e.y >= nL) {
+            atomicOr(err, kErrRange);
+            continue;
+        }
+        uint32_t gu, gv;
+        gids(e.x, e.y, nU, nL, flags, gu, gv);
+        atomicAdd(&deg[gu], 1u);
+        atomicAdd(&deg[gv], 1u);
+    }
+}
+
+__global__ void k_iota(uint32_t *a, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        a[i] = i;
+}
+
+// order[r] = global id of rank r (sorted by degree, stable on id => ties by
+// id); deg_sorted[r] = its degree.
+__global__ void k_rank(const uint32_t *order, const uint32_t *deg_sorted, uint32_t n,
+                       uint32_t *rank, uint64_t *degr) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        rank[order[r]] = r;
+        degr[r] = deg_sorted[r];
+    }
+}
+
+__global__ void k_arcs(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
+                       const uint32_t *rank, uint32_t n, uint64_t *keys, uint32_t *vals) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        int2 e = reinterpret_cast<const int2 *>(edges)[i];
+        if (e.x < 0 || e.y < 0 || (uint32_t)e.x >= nU || (uint32_t)e.y >= nL) {
+            keys[2 * i] = keys[2 * i + 1] = 0;  // flagged by k_degree; call fails
+            vals[2 * i] = vals[2 * i + 1] = (uint32_t)i;
+            continue;
+        }
+        uint32_t gu, gv;
+        gids(e.x, e.y, nU, nL, flags, gu, gv);
+        uint64_t ru = rank[gu], rv = rank[gv];
+        keys[2 * i] = ru * n + rv;
+        vals[2 * i] = (uint32_t)i;
+        keys[2 * i + 1] = rv * n + ru;
+        vals[2 * i + 1] = (uint32_t)i;
+    }
+}
+
+__global__ void k_csr_fill(const uint64_t *keys, const uint32_t *vals, uint64_t na, uint32_t n,
+                           uint32_t *adj, uint32_t *eid, uint32_t *err) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < na;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t k = keys[j];
+        adj[j] = (uint32_t)(k % n);
+        eid[j] = vals[j];
+        if (j > 0 && keys[j - 1] == k) atomicOr(err, kErrDup);
+    }
+}
+
+__device__ __forceinline__ uint32_t lower_bound(const uint32_t *a, uint32_t len, uint32_t key) {
+    uint32_t lo = 0, hi = len;
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Warp per vertex u: hv[u] = |{v in N(u): v < u}|; for those arcs
+// pl = |{w in N(v): w < u}|; wv[u] = sum of pl (wedges started at u).
+__global__ void k_wedge_prefix(const uint64_t *off, const uint32_t *adj, uint32_t n, uint32_t *hv,
+                               uint32_t *pl, uint64_t *wv) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t u = warp; u < n; u += nwarps) {
+        uint64_t a = off[u];
+        uint32_t d = (uint32_t)(off[u + 1] - a);
+        uint32_t h = lower_bound(adj + a, d, u);
+        uint64_t acc = 0;
+        for (uint32_t i = lane; i < d; i += 32) {
+            uint32_t p = 0;
+            if (i < h) {
+                uint32_t v = adj[a + i];
+                uint64_t b = off[v];
+                p = lower_bound(adj + b, (uint32_t)(off[v + 1] - b), u);
+            }
+            pl[a + i] = p;
+            acc += p;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            hv[u] = h;
+            wv[u] = acc;
+        }
+    }
+}
+
+inline unsigned grid_for(uint64_t items, int threads, unsigned cap = 152 * 32) {
+    uint64_t g = (items + threads - 1) / threads;
+    if (g == 0) g = 1;
+    return (unsigned)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
+                      Csr &g, uint32_t *err_word, Alloc &al) {
+    const uint32_t n = nU + nL;
+    g.n = n;
+    g.m = m;
+    uint32_t *deg = al.get<uint32_t>(n);
+    uint32_t *order = al.get<uint32_t>(n);
+    uint32_t *tk = al.get<uint32_t>(n);
+    uint32_t *tv = al.get<uint32_t>(n);
+    uint32_t *rank = al.get<uint32_t>(n);
+    uint64_t *degr = al.get<uint64_t>((size_t)n + 1);
+    g.off = al.get<uint64_t>((size_t)n + 1);
+    if (al.err != cudaSuccess) return al.err;
+    al.mark(kPhCsr, false);
+    BT_CUDA(cudaMemsetAsync(deg, 0, sizeof(uint32_t) * n, al.stream));
+    k_degree<<<grid_for(m, 256), 256, 0, al.stream>>>(d_edges, m, nU, nL, flags, deg, err_word);
+    al.launches++;
+    k_iota<<<grid_for(n, 256), 256, 0, al.stream>>>(order, n);
+    al.launches++;
+    // degrees are <= max(nU, nL); a stable sort on degree keeps ties in id order
+    BT_CUDA(radix_sort_u32(deg, order, tk, tv, n, bits_for(nU > nL ? nU : nL), al));
+    // deg now holds the degrees in rank order
+    BT_CUDA(cudaMemsetAsync(degr, 0, sizeof(uint64_t) * ((size_t)n + 1), al.stream));
+    k_rank<<<grid_for(n, 256), 256, 0, al.stream>>>(order, deg, n, rank, degr);
+    al.launches++;
+    BT_CUDA(cudaGetLastError());
+    al.put(tk);
+    al.put(tv);
+    // off = exclusive scan of degree by rank
+    BT_CUDA(exclusive_scan_u64(degr, g.off, (size_t)n + 1, nullptr, al));
+
+    const uint64_t na = 2 * m;
+    uint64_t *keys = al.get<uint64_t>(na);
+    uint32_t *vals = al.get<uint32_t>(na);
+    uint64_t *k2 = al.get<uint64_t>(na);
+    uint32_t *v2 = al.get<uint32_t>(na);
+    if (al.err != cudaSuccess) return al.err;
+    k_arcs<<<grid_for(m, 256), 256, 0, al.stream>>>(d_edges, m, nU, nL, flags, rank, n, keys, vals);
+    al.launches++;
+    BT_CUDA(radix_sort_u64(keys, vals, k2, v2, na, bits_for((uint64_t)n * n - 1), al));
+    al.put(k2);
+    al.put(v2);
+    g.adj = al.get<uint32_t>(na);
+    g.eid = al.get<uint32_t>(na);
+    g.pl = al.get<uint32_t>(na);
+    g.hv = al.get<uint32_t>(n);
+    g.wv = al.get<uint64_t>(n);
+    if (al.err != cudaSuccess) return al.err;
+    k_csr_fill<<<grid_for(na, 256), 256, 0, al.stream>>>(keys, vals, na, n, g.adj, g.eid, err_word);
+    al.launches++;
+    al.put(keys);
+    al.put(vals);
+    k_wedge_prefix<<<grid_for((uint64_t)n * 32, 256), 256, 0, al.stream>>>(g.off, g.adj, n, g.hv,
+                                                                           g.pl, g.wv);
+    al.launches++;
+    al.mark(kPhCsr, true);
+    al.put(deg);
+    al.put(order);
+    al.put(rank);
+    al.put(degr);
+    return cudaGetLastError();
+}
+
+void free_csr(Csr &g, Alloc &al) {
+    al.put(g.off);
+    al.put(g.adj);
+    al.put(g.eid);
+    al.put(g.pl);
+    al.put(g.hv);
+    al.put(g.wv);
+    g = Csr{};
+}
+
+}  // namespace bt
