@@ -185,7 +185,9 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     uint32_t *pair_bloom, uint32_t *inc, uint32_t *queue) {
     __shared__ Chunk ch;
     __shared__ uint32_t s_q;
-    __shared__ uint32_t s_nb, s_np;
+    // bloom count (high 32 bits) and pair count (low 32 bits) of the vertex,
+    // advanced by one atomic so that pair ranges follow bloom ids
+    __shared__ unsigned long long s_alloc;
     uint32_t *cnt = cnt_all + (size_t)blockIdx.x * n;
     uint32_t *aux = aux_all + (size_t)blockIdx.x * n;
     for (;;) {
@@ -196,10 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(
         const uint32_t h = hv[u];
         const uint64_t bb = bloom_base[u];
         const uint64_t pb = pair_base[u];
-        if (threadIdx.x == 0) {
-            s_nb = 0;
-            s_np = 0;
-        }
+        if (threadIdx.x == 0) s_alloc = 0;
         pass_count(ch, off, adj, eid, pl, a, h, cnt);
         // claim: one thread per bloom allocates its id and pair range
         for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
@@ -210,8 +209,9 @@ __global__ void __launch_bounds__(kThreads) k_emit(
                 uint32_t w = adj[arc];
                 uint32_t c = ld_cg(&cnt[w]);
                 if (c >= 2 && atomicCAS(&aux[w], 0u, 1u) == 0u) {
-                    uint32_t j = atomicAdd(&s_nb, 1u);
-                    uint32_t p = atomicAdd(&s_np, c);
+                    unsigned long long old = atomicAdd(&s_alloc, (1ull << 32) | c);
+                    uint32_t j = (uint32_t)(old >> 32);
+                    uint32_t p = (uint32_t)old;
                     uint64_t B = bb + j;
                     bloom_k[B] = c;
                     bloom_off[B] = (uint32_t)(pb + p);

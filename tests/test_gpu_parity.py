@@ -83,8 +83,10 @@ def test_paper_example_index_fig6(h):
 def check_index_invariants(h, edges, nU, nL, sup, flags=0):
     st = bt.bt_build_index(h, edges, nU, nL, flags)
     k, first, pairs, deg = bt.bt_index_export(h, st, len(edges))
-    # Lemma 7: a k-bloom is k priority-obeyed wedges (pairs)
+    # Lemma 7: a k-bloom is k priority-obeyed wedges (pairs); the layout keeps
+    # each bloom's pairs contiguous and in bloom order (the peel relies on it)
     sizes = np.diff(np.append(first.astype(np.int64), st["n_bloom_wedges"]))
+    np.testing.assert_array_equal(sizes, k.astype(np.int64))
     order = np.argsort(first)
     assert (np.sort(sizes[order]) >= 2).all() if len(k) else True
     assert int(k.astype(np.int64).sum()) == st["n_bloom_wedges"]
