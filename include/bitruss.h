@@ -54,7 +54,8 @@ typedef enum {
     BT_ERR_OVERFLOW = 5,    /* a count exceeds its storage type (e.g. phi > 2^32-1) */
     BT_ERR_NOCONVERGE = 6,  /* peeling exceeded its round limit */
     BT_ERR_CUDA = 7,        /* a CUDA runtime call failed */
-    BT_ERR_STATE = 8        /* call needs state the handle does not hold */
+    BT_ERR_STATE = 8,       /* call needs state the handle does not hold */
+    BT_ERR_TOO_LARGE = 9    /* graph exceeds bt_count_support_static's fixed capacity */
 } bt_status;
 
 /* flags */
@@ -174,6 +175,33 @@ int bt_profile_enable(bt_handle *h, int on);
  * on h (zeros for phases it did not run, and times only when profiling was
  * enabled).  Errors: BT_ERR_ARG. */
 int bt_profile_read(const bt_handle *h, bt_profile *out);
+
+/*
+ * Allocation-free variant of bt_count_support.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * around a library call -- hosts that own all GPU memory through their own
+ * pool and accounting (often under a hard cap), and latency-critical loops
+ * that must not trigger the device-wide synchronisation cudaMalloc/cudaFree
+ * may cause.  It runs the same CSR-build and wedge-count kernels, taking all
+ * scratch from one fixed 48 MiB device array inside the library; it calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   d_edges:        device pointer, int32 pairs as for bt_count_support.
+ *   d_support_out:  device pointer, uint64[m].
+ *   flags:          0 or BT_TIE_LOWER_FIRST (pointers are always device).
+ *   cuda_stream:    cudaStream_t to run on (NULL = legacy default stream);
+ *                   the call synchronises it before returning.
+ * Capacity: m <= 262,144 edges and nU + nL <= 131,072 vertices; larger
+ * graphs return BT_ERR_TOO_LARGE.  Runs on the current CUDA device.  The
+ * array lives in every GPU that loads the library until the process exits;
+ * the first call on a device looks up its address (call it once before any
+ * stream capture).  All calls share the array and it keeps the last call's
+ * contents (the call clears what must start at zero); calls whose GPU work
+ * overlaps race on it and must be ordered by the caller.
+ * Errors: BT_ERR_ARG, BT_ERR_RANGE, BT_ERR_DUP, BT_ERR_TOO_LARGE, BT_ERR_CUDA
+ * (no handle, so no message).  m == 0 returns BT_OK.
+ */
+int bt_count_support_static(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL,
+                            uint64_t *d_support_out, uint32_t flags, void *cuda_stream);
 
 /*
  * Device bytes a bt_decompose of this graph needs (host computation, O(m)

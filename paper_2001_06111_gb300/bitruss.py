@@ -26,12 +26,13 @@ BT_ERR_OVERFLOW = 5
 BT_ERR_NOCONVERGE = 6
 BT_ERR_CUDA = 7
 BT_ERR_STATE = 8
+BT_ERR_TOO_LARGE = 9
 BT_DEVICE_PTRS = 0x1
 BT_TIE_LOWER_FIRST = 0x2
 
 EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_build_index",
             "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
-            "bt_profile_read")
+            "bt_profile_read", "bt_count_support_static")
 
 
 class BitrussError(RuntimeError):
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH):
         lib.bt_build_index.argtypes = [P, P, U64, U32, U32, ctypes.POINTER(IndexStats), U32]
         lib.bt_index_export.argtypes = [P, P, P, P]
         lib.bt_decompose.argtypes = [P, P, U64, U32, U32, P, P, ctypes.POINTER(PeelStats), U32]
+        lib.bt_count_support_static.argtypes = [P, U64, U32, U32, P, U32, P]
         lib.bt_profile_enable.argtypes = [P, I]
         lib.bt_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         lib.bt_estimate_bytes.argtypes = [P, U64, U32, U32, U32, ctypes.POINTER(U64),
@@ -225,6 +227,21 @@ def bt_decompose(h: Handle, edges, nU: int, nL: int, support_out=None, phi_out=N
     st = PeelStats()
     _check(h, load().bt_decompose(h.ptr, ptr, m, nU, nL, sptr, pptr, ctypes.byref(st), flags | f))
     return sup, phi, _as_dict(st)
+
+
+def bt_count_support_static(d_edges, nU: int, nL: int, d_support_out, flags: int = 0,
+                            stream=None) -> None:
+    """Allocation-free support count on device buffers (CUDA torch tensors):
+    scratch comes from a fixed array inside the library, for callers that
+    cannot allocate device memory.  Raises BitrussError on failure."""
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    m = int(d_edges.shape[0])
+    rc = load().bt_count_support_static(d_edges.data_ptr(), m, nU, nL, d_support_out.data_ptr(),
+                                        flags, s)
+    if rc != BT_OK:
+        raise BitrussError(rc, "bt_count_support_static failed")
 
 
 def bt_profile_enable(h: Handle, on: bool = True):

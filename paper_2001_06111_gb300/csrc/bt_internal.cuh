@@ -34,6 +34,10 @@ struct Alloc {
     cudaError_t err = cudaSuccess;
     uint64_t launches = 0;
     Prof *prof = nullptr;
+    // Optional fixed arena (set only by the allocation-free entry point):
+    // get() then bump-allocates inside it and put() does nothing.
+    unsigned char *arena = nullptr;
+    size_t arena_size = 0, arena_used = 0;
     void mark(int phase, bool end) {
         if (prof && prof->on) {
             cudaEventRecord(prof->ev[2 * phase + (end ? 1 : 0)], stream);
@@ -46,11 +50,20 @@ struct Alloc {
         void *p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
+        if (arena) {
+            size_t off = (arena_used + 255) & ~size_t(255);
+            if (off + bytes > arena_size) {
+                err = cudaErrorMemoryAllocation;
+                return nullptr;
+            }
+            arena_used = off + bytes;
+            return reinterpret_cast<T *>(arena + off);
+        }
         err = cudaMallocFromPoolAsync(&p, bytes, pool, stream);
         return err == cudaSuccess ? static_cast<T *>(p) : nullptr;
     }
     void put(void *p) {
-        if (p) cudaFreeAsync(p, stream);
+        if (p && !arena) cudaFreeAsync(p, stream);
     }
 };
 
