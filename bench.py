@@ -29,8 +29,13 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(name="chunglu-200k-80k-2M-cap20k", nU=200000, nL=80000, m=2000000, gammaU=2.1,
-                gammaL=2.4, cap=20000, seed=2)
+WORKLOADS = {
+    "medium": dict(name="chunglu-200k-80k-2M-cap20k", nU=200000, nL=80000, m=2000000, gammaU=2.1,
+                   gammaL=2.4, cap=20000, seed=2),
+    "small": dict(name="chunglu-2k-1.5k-20k", nU=2000, nL=1500, m=20000, gammaU=2.2, gammaL=2.5,
+                  cap=0, seed=1),
+}
+WORKLOAD = WORKLOADS["medium"]
 METRIC = "edges decomposed/s"
 UNIT = "edges/s"
 CPU_SAMPLE_FRAC = 0.3   # vertex-induced sample for the oracle baseline
@@ -111,12 +116,37 @@ def dist_env():
 
 
 def algorithmic_bytes(p):
-    """Per-launch algorithmic bytes of the count and emit kernels (figures per
-    wedge / bloom wedge / bloom / edge as stated in the design notes)."""
+    """Per-launch algorithmic bytes of the count, emit and peel kernels
+    (W wedges, W2 bloom wedges, NB blooms, m edges; the peel's link visits,
+    pair-slot visits and support updates are counted by the library)."""
     W, W2, NB, m = p["n_wedges"], p["n_bloom_wedges"], p["n_blooms"], p["n_edges"]
     count = 12 * W + 8 * W2 + 20 * m
     emit = 8 * W + 20 * W2 + 12 * NB
-    return {"count": count, "emit": emit}
+    peel = 25 * p["link_visits"] + 9 * p["pair_slots"] + 16 * p["support_updates"]
+    return {"count": count, "emit": emit, "peel": peel}
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, or
+    None when there is none or the kernel source changed since the capture."""
+    import hashlib
+    import re
+    src = {"peel": "peel.cu", "count": "count.cu", "emit": "count.cu"}.get(kernel)
+    prof = os.path.join(ROOT, "profiles", f"k_{kernel}-{WORKLOAD_PROFILE_TAG.get(workload, '')}.md")
+    if not src or not os.path.exists(prof):
+        return None
+    text = open(prof).read()
+    m_t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+    m_h = re.search(r"sha256 \(csrc/[a-z_.]+\) \| ([0-9a-f]{64})", text)
+    if not m_t or not m_h:
+        return None
+    with open(os.path.join(ROOT, "paper_2001_06111_gb300", "csrc", src), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != m_h.group(1):
+            return None
+    return int(m_t.group(1))
+
+
+WORKLOAD_PROFILE_TAG = {"medium": "chunglu-2M", "small": "chunglu-20k"}
 
 
 def run_reference(args):
@@ -175,7 +205,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS),
+                    help="medium (default) is the benchmark workload; small is for profiling")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -264,7 +298,7 @@ def main():
     med = lambda key: statistics.median(p[key] for p in profs)  # noqa: E731
     ab = algorithmic_bytes(p0)
     peak, peak_kind = load_peaks()
-    kern = {"count": med("count_ms"), "emit": med("emit_ms")}
+    kern = {"count": med("count_ms"), "emit": med("emit_ms"), "peel": med("peel_ms")}
     dom = max(kern, key=kern.get)
     achieved = ab[dom] / (kern[dom] / 1e3) / 1e9
     line = {
@@ -279,10 +313,12 @@ def main():
         "phases_ms": {"csr": med("csr_ms"), "count": med("count_ms"), "emit": med("emit_ms"),
                       "peel": med("peel_ms"), "call": med("total_ms")},
         "work": {k: p0[k] for k in ("n_wedges", "n_bloom_wedges", "n_blooms", "rounds", "levels",
-                                    "support_updates")},
+                                    "support_updates", "pair_slots", "link_visits")},
+        "kernels_gbs": {k: ab[k] / (kern[k] / 1e3) / 1e9 for k in kern if kern[k] > 0},
         "roofline": {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "algorithmic_bytes": ab[dom], "traffic": None},
+                     "algorithmic_bytes": ab[dom],
+                     "traffic": measured_traffic(dom, args.workload)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 12 * m, "steps": e2e_steps},
         "gpu_launches": int(sum(p["launches"] for p in profs)),

@@ -101,6 +101,8 @@ typedef struct {
     uint64_t launches; /* kernels this call launched */
     uint64_t n_edges, n_vertices, n_wedges, n_bloom_wedges, n_blooms;
     uint64_t rounds, levels, support_updates;
+    uint64_t pair_slots;   /* bloom pair slots the peel's bloom phase visited */
+    uint64_t link_visits;  /* edge-bloom links the peel's incidence phase visited */
 } bt_profile;
 
 /*

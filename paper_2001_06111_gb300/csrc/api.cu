@@ -424,6 +424,8 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
         h->last.rounds = pr.rounds;
         h->last.levels = pr.levels;
         h->last.support_updates = pr.updates;
+        h->last.pair_slots = pr.slots;
+        h->last.link_visits = 2 * h->index.w2;
     }
     cudaStreamSynchronize(h->stream);
     return rc;

@@ -2,13 +2,13 @@
 // Alg. 5, BiT-BU++; the <= k frontier rule of Alg. 4).
 //
 // One round removes the batch S = {unassigned e : support(e) <= k} at once:
-//   incidence pass (Alg. 5, the loop over e in S and B in N_I(e)):
+//   incidence phase (Alg. 5, the loop over e in S and B in N_I(e)):
 //     every live twin pair of a bloom B that holds an edge of S dies once;
 //     C(B) counts the dead pairs.  When both twins are in S the one with the
 //     smaller edge id owns the pair, so a pair is counted once (the example of
 //     Section V-B: three twin pairs of B0 drop its bloom number to 0).  A twin
 //     outside S loses all k_B - 1 butterflies it had in B (Lemma 2).
-//   bloom pass (Alg. 5, the loop over blooms with C(B) > 0):
+//   bloom phase (Alg. 5, the loop over blooms with C(B) > 0):
 //     every edge of a surviving pair of B loses C(B) butterflies (one per
 //     dead pair); then k_B -= C(B), so the bloom keeps C(k_B - C, 2)
 //     butterflies (Lemma 1).
@@ -16,139 +16,407 @@
 // k only grows: when no unassigned edge has support <= k, k jumps to the
 // minimum remaining support (the batch-edge rule of Lemma 9).  Supports are
 // decremented without the max(MBS, .) clamp of Alg. 5; an edge that drops to
-// or below k is simply taken by the next round with the same k, which gives
-// the same phi.  An edge joins the next batch exactly when one decrement
-// carries its support from above k to <= k, so rounds inside a level never
-// rescan all edges.
+// or below k is taken by the next round with the same k, which gives the same
+// phi.  An edge joins the next batch exactly when one decrement carries its
+// support from above k to <= k, so rounds inside a level never rescan edges.
+//
+// The whole loop runs in one persistent cooperative kernel (one block per SM
+// slot the occupancy allows).  Phases are separated by a grid barrier whose
+// wait is bounded by a timer; on timeout the kernel raises an error word and
+// every block returns.  Work is split into items of at most kSeg entries: an
+// edge of S with a long link list becomes several incidence items, and a
+// touched bloom with many pairs several bloom items, so no warp straggles on
+// a hub.  Counters and work lists are double-buffered by round parity, which
+// leaves two barriers per round.  Data written by other blocks during the
+// kernel is read with L2 (.cg) loads.
 #include "bt_device.cuh"
 #include "bt_internal.cuh"
 
 namespace bt {
 namespace {
 
-struct Ctrl {
-    unsigned long long minsup;
+constexpr int kPeelThreads = 1024;
+constexpr uint32_t kSeg = 32;                     // entries per work item (one per lane)
+constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+constexpr uint32_t kErrBarrier = 1u;
+constexpr uint32_t kErrRounds = 2u;
+constexpr uint32_t kErrPeelOverflow = 4u;
+
+struct Ctl {
+    unsigned long long bar_count;  // barrier arrivals (monotonic within a launch)
+    unsigned int err;
+    unsigned int pad0;
+    unsigned int n_items[2];  // incidence items per round parity
+    unsigned int n_edges[2];  // frontier edges per round parity
+    unsigned int n_bseg[3];   // bloom items per round mod 3
+    unsigned int n_alive[2];  // alive list sizes (ping-pong)
+    unsigned int n_near[2];   // near-window list sizes (ping-pong)
+    unsigned int pad1;
+    unsigned long long minsup;   // level-jump minimum over the near window
+    unsigned long long minsup2;  // minimum over all alive edges (window rebuild)
     unsigned long long updates;
-    uint32_t n_next;
-    uint32_t n_touched;
-    uint32_t n_collect;
-    uint32_t pad;
+    unsigned long long slots;  // bloom pair slots visited by the bloom phase
+    unsigned long long rounds;
+    unsigned long long levels;
+    unsigned long long windows;
+    unsigned long long kfinal;
 };
 
-__global__ void k_peel_init(const uint64_t *support, uint64_t m, long long *sup, uint32_t *state) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        sup[i] = (long long)support[i];
-        state[i] = kAlive;
-    }
+struct PeelArgs {
+    uint64_t m;
+    const uint64_t *inc_off;
+    const uint32_t *inc;
+    const uint2 *pairs;
+    const uint32_t *pair_bloom;
+    const uint32_t *bloom_off;
+    long long *sup;
+    uint32_t *state;
+    uint32_t *phi;
+    uint8_t *pair_alive;
+    uint32_t *bk;
+    uint32_t *Cb[3];
+    uint4 *items[2];   // (edge, first link lo, first link hi, count | head flag << 31)
+    uint4 *bseg[3];    // (bloom, first pair, count, head flag)
+    uint32_t *alive[2];
+    uint32_t *near[2];
+    uint64_t item_cap;
+    Ctl *ctl;
+    uint64_t round_limit;
+};
+
+// Loop state every thread keeps identically (derived from values read after
+// grid barriers).
+struct Lvl {
+    long long k;    // current level
+    long long khi;  // top of the near window: alive edges with support < khi are listed
+    uint32_t nq;    // current near list
+};
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-__global__ void k_min_alive(const uint32_t *state, const long long *sup, uint64_t m, Ctrl *ctrl) {
-    unsigned long long best = ~0ull;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        if (state[i] == kAlive) {
-            unsigned long long s = (unsigned long long)sup[i];
-            best = s < best ? s : best;
+__device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned int ldcg_ui(const unsigned int *p) { return __ldcg(p); }
+__device__ __forceinline__ long long ldcg_ll(const long long *p) { return __ldcg(p); }
+__device__ __forceinline__ uint8_t ldcg_u8(const uint8_t *p) {
+    unsigned short v;
+    asm volatile("ld.global.cg.u8 %0, [%1];" : "=h"(v) : "l"(p));
+    return (uint8_t)v;
+}
+
+// Grid-wide barrier over all blocks of a cooperative launch.  Arrivals go
+// to one monotonic counter (release); barrier number b completes when the
+// counter reaches (b + 1) * gridDim.x, which every block polls (acquire).
+// Returns false when the wait timed out or another block raised an error.
+__device__ __forceinline__ void arrive_release(unsigned long long *p) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(p) : "memory");
+}
+__device__ __forceinline__ unsigned long long load_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no) {
+    __syncthreads();
+    __shared__ int s_ok;
+    const unsigned long long target = (bar_no + 1) * gridDim.x;
+    ++bar_no;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        arrive_release(&ctl->bar_count);
+        if (load_acquire(&ctl->bar_count) < target) {
+            const unsigned long long t0 = now_ns();
+            unsigned int spins = 0;
+            while (load_acquire(&ctl->bar_count) < target) {
+                if (((++spins) & 63u) == 0) {
+                    if (*(volatile unsigned int *)&ctl->err) {
+                        ok = 0;
+                        break;
+                    }
+                    if (now_ns() - t0 > kBarrierTimeoutNs) {
+                        atomicOr(&ctl->err, kErrBarrier);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
         }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
-        best = y < best ? y : best;
+        s_ok = ok;
     }
-    if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&ctrl->minsup, best);
+    __syncthreads();
+    return s_ok != 0;
 }
 
-__global__ void k_collect(uint32_t *state, const long long *sup, uint64_t m, long long k,
-                          uint32_t round, uint32_t *S, Ctrl *ctrl) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        if (state[i] == kAlive && sup[i] <= k) {
-            state[i] = round;
-            S[atomicAdd(&ctrl->n_collect, 1u)] = (uint32_t)i;
+// Queue edge e (links [ib, ie)) for the round `next_round`: one incidence
+// item per kSeg links, each carrying its link range.
+__device__ __forceinline__ void push_edge(const PeelArgs &a, uint32_t e, uint32_t dst,
+                                          uint32_t next_round, uint64_t ib, uint64_t ie) {
+    a.state[e] = next_round;
+    const uint64_t d = ie - ib;
+    const uint32_t nseg = d == 0 ? 1u : (uint32_t)((d + kSeg - 1) / kSeg);
+    const uint32_t base = atomicAdd(&a.ctl->n_items[dst], nseg);
+    for (uint32_t s = 0; s < nseg; ++s) {
+        const uint64_t j = ib + (uint64_t)s * kSeg;
+        const uint64_t left = d - (uint64_t)s * kSeg;
+        const uint32_t cnt = (uint32_t)(left < kSeg ? left : kSeg);
+        a.items[dst][base + s] =
+            make_uint4(e, (uint32_t)j, (uint32_t)(j >> 32), cnt | (s == 0 ? 0x80000000u : 0u));
+    }
+    atomicAdd(&a.ctl->n_edges[dst], 1u);
+}
+
+__device__ __forceinline__ void push_near(const PeelArgs &a, uint32_t e, uint32_t nq) {
+    a.near[nq][atomicAdd(&a.ctl->n_near[nq], 1u)] = e;
+}
+
+// Subtract dec from support(e).  Queue e for the next round when this takes
+// it from > k to <= k, and list it in the near window when it falls below khi.
+__device__ __forceinline__ void decrement(const PeelArgs &a, uint32_t e, long long dec, const Lvl &L,
+                                          uint32_t dst, uint32_t next_round, bool have_range,
+                                          uint64_t ib, uint64_t ie) {
+    const long long old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.sup[e]),
+                                               (unsigned long long)(-dec));
+    const long long now = old - dec;
+    if (old > L.k && now <= L.k) {
+        if (!have_range) {
+            ib = a.inc_off[e];
+            ie = a.inc_off[e + 1];
         }
-}
-
-// Subtract dec from the support of e; queue e for the next round when this
-// decrement takes it from above k to <= k.
-__device__ __forceinline__ void decrement(long long *sup, uint32_t *state, uint32_t *S_next,
-                                          Ctrl *ctrl, uint32_t e, long long dec, long long k,
-                                          uint32_t round) {
-    long long old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&sup[e]),
-                                         (unsigned long long)(-dec));
-    if (old > k && old - dec <= k) {
-        state[e] = round + 1;
-        S_next[atomicAdd(&ctrl->n_next, 1u)] = e;
+        push_edge(a, e, dst, next_round, ib, ie);
     }
+    if (old >= L.khi && now < L.khi) push_near(a, e, L.nq);
 }
 
-// Warp per edge of S.
-__global__ void k_incidence(const uint32_t *__restrict__ S, uint32_t nS, uint32_t round,
-                            long long k, const uint64_t *__restrict__ inc_off,
-                            const uint32_t *__restrict__ inc, const uint2 *__restrict__ pairs,
-                            const uint32_t *__restrict__ pair_bloom, uint8_t *pair_alive,
-                            const uint32_t *__restrict__ bk, uint32_t *C, uint32_t *touched,
-                            long long *sup, uint32_t *state, uint32_t *S_next, uint32_t *phi,
-                            Ctrl *ctrl) {
+__device__ __forceinline__ long long window_top(long long kmin) {
+    long long w = kmin / 4;
+    return kmin + (w < 16 ? 16 : w);
+}
+
+__global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long upd = 0;
-    for (uint32_t i = warp; i < nS; i += nwarps) {
-        const uint32_t e = S[i];
-        if (lane == 0) phi[e] = (uint32_t)k;
-        const uint64_t b = inc_off[e], end = inc_off[e + 1];
-        for (uint64_t j = b + lane; j < end; j += 32) {
-            const uint32_t p = inc[j];
-            if (!pair_alive[p]) continue;
-            const uint2 pr = pairs[p];
-            const uint32_t t = pr.x == e ? pr.y : pr.x;
-            const uint32_t st = state[t];
-            if (st == round && t < e) continue;  // twin in S with smaller id owns the pair
-            pair_alive[p] = 0;
-            const uint32_t B = pair_bloom[p];
-            if (atomicAdd(&C[B], 1u) == 0u) touched[atomicAdd(&ctrl->n_touched, 1u)] = B;
-            if (st != round) {
-                const long long dec = (long long)bk[B] - 1;
-                if (dec > 0) {
-                    decrement(sup, state, S_next, ctrl, t, dec, k, round);
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    Ctl *ctl = a.ctl;
+    uint64_t remaining = a.m;
+    uint32_t round = 0;
+    Lvl L{0, 0, 0};
+    uint32_t ap = 0;  // current alive list
+    bool level_jump = true;
+    unsigned long long upd = 0, slots = 0;
+    unsigned long long bar_no = 0;  // barriers passed (identical in every block)
+
+    while (remaining > 0) {
+        const uint32_t par = round & 1u, np = par ^ 1u;
+        const uint32_t c3 = round % 3u;
+        if (round > a.round_limit) {
+            if (gtid == 0) atomicOr(&ctl->err, kErrRounds);
+            break;
+        }
+        if (level_jump) {
+            // L1: minimum over the near window, compacting it
+            {
+                const uint32_t nn = ldcg_ui(&ctl->n_near[L.nq]);
+                unsigned long long best = ~0ull;
+                for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < nn; i0 += nthreads) {
+                    const uint32_t i = i0 + threadIdx.x;
+                    bool keep = false;
+                    uint32_t e = 0;
+                    if (i < nn) {
+                        e = ldcg_u32(&a.near[L.nq][i]);
+                        if (ldcg_u32(&a.state[e]) == kAlive) {
+                            keep = true;
+                            const unsigned long long sv = (unsigned long long)ldcg_ll(&a.sup[e]);
+                            best = sv < best ? sv : best;
+                        }
+                    }
+                    const unsigned int mask = __ballot_sync(0xffffffffu, keep);
+                    if (mask) {
+                        unsigned int base = 0;
+                        if (lane == 0) base = atomicAdd(&ctl->n_near[L.nq ^ 1u], (unsigned)__popc(mask));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (keep) a.near[L.nq ^ 1u][base + __popc(mask & ((1u << lane) - 1u))] = e;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+                    best = y < best ? y : best;
+                }
+                if (lane == 0 && best != ~0ull) atomicMin(&ctl->minsup, best);
+            }
+            if (!grid_barrier(ctl, bar_no)) break;
+            unsigned long long mn = __ldcg(&ctl->minsup);
+            L.nq ^= 1u;
+            if (gtid == 0) ctl->n_near[L.nq ^ 1u] = 0;
+            if (mn == ~0ull) {
+                // the window holds no alive edge: rebuild it from all alive edges.
+                // W1: overall minimum, compacting the alive list
+                const uint32_t na = ldcg_ui(&ctl->n_alive[ap]);
+                unsigned long long best = ~0ull;
+                for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < na; i0 += nthreads) {
+                    const uint32_t i = i0 + threadIdx.x;
+                    bool keep = false;
+                    uint32_t e = 0;
+                    if (i < na) {
+                        e = ldcg_u32(&a.alive[ap][i]);
+                        if (ldcg_u32(&a.state[e]) == kAlive) {
+                            keep = true;
+                            const unsigned long long sv = (unsigned long long)ldcg_ll(&a.sup[e]);
+                            best = sv < best ? sv : best;
+                        }
+                    }
+                    const unsigned int mask = __ballot_sync(0xffffffffu, keep);
+                    if (mask) {
+                        unsigned int base = 0;
+                        if (lane == 0) base = atomicAdd(&ctl->n_alive[ap ^ 1u], (unsigned)__popc(mask));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (keep) a.alive[ap ^ 1u][base + __popc(mask & ((1u << lane) - 1u))] = e;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+                    best = y < best ? y : best;
+                }
+                if (lane == 0 && best != ~0ull) atomicMin(&ctl->minsup2, best);
+                if (!grid_barrier(ctl, bar_no)) break;
+                mn = __ldcg(&ctl->minsup2);
+                if (mn == ~0ull) break;  // no alive edge: cannot happen while remaining > 0
+                L.khi = window_top((long long)mn);
+                ap ^= 1u;
+                if (gtid == 0) ctl->n_alive[ap ^ 1u] = 0;
+                // W2: list every alive edge below the new window top
+                const uint32_t na2 = ldcg_ui(&ctl->n_alive[ap]);
+                for (uint32_t i = gtid; i < na2; i += nthreads) {
+                    const uint32_t e = ldcg_u32(&a.alive[ap][i]);
+                    if (ldcg_ll(&a.sup[e]) < L.khi) push_near(a, e, L.nq);
+                }
+                if (gtid == 0) atomicAdd(&ctl->windows, 1ull);
+                if (!grid_barrier(ctl, bar_no)) break;
+                if (gtid == 0) ctl->minsup2 = ~0ull;
+            }
+            if ((long long)mn > L.k) L.k = (long long)mn;
+            if ((unsigned long long)L.k > 0xFFFFFFFFull) {
+                if (gtid == 0) atomicOr(&ctl->err, kErrPeelOverflow);
+                break;
+            }
+            // L2: the batch is every window edge with support <= k
+            const uint32_t nn2 = ldcg_ui(&ctl->n_near[L.nq]);
+            for (uint32_t i = gtid; i < nn2; i += nthreads) {
+                const uint32_t e = ldcg_u32(&a.near[L.nq][i]);
+                if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k)
+                    push_edge(a, e, par, round, a.inc_off[e], a.inc_off[e + 1]);
+            }
+            if (gtid == 0) atomicAdd(&ctl->levels, 1ull);
+            if (!grid_barrier(ctl, bar_no)) break;
+            if (gtid == 0) ctl->minsup = ~0ull;
+        }
+
+        // ---------------- incidence phase
+        uint32_t *C = a.Cb[c3];
+        // read before the barrier below: block 0 clears it in the bloom phase
+        const uint32_t n_edges = ldcg_ui(&ctl->n_edges[par]);
+        {
+            const uint32_t n_items = ldcg_ui(&ctl->n_items[par]);
+            const bool spec = gwarp < a.item_cap;
+            uint4 it0 = spec ? __ldcg(&a.items[par][gwarp]) : make_uint4(0, 0, 0, 0);
+            if (gtid == 0) ctl->n_bseg[(c3 + 1u) % 3u] = 0;
+            for (uint32_t i = gwarp; i < n_items; i += nwarps) {
+                const uint4 it = i == gwarp ? it0 : __ldcg(&a.items[par][i]);
+                const uint32_t e = it.x;
+                if ((it.w >> 31) && lane == 0) a.phi[e] = (uint32_t)L.k;
+                const uint32_t cnt = it.w & 0x7FFFFFFFu;
+                if ((uint32_t)lane >= cnt) continue;
+                const uint64_t j = ((uint64_t)it.z << 32 | it.y) + lane;
+                const uint32_t p = a.inc[j];
+                const uint8_t alive = ldcg_u8(&a.pair_alive[p]);
+                const uint2 pr = a.pairs[p];
+                const uint32_t B = a.pair_bloom[p];
+                if (!alive) continue;
+                const uint32_t t = pr.x == e ? pr.y : pr.x;
+                const uint32_t st = ldcg_u32(&a.state[t]);
+                const uint32_t bkB = ldcg_u32(&a.bk[B]);
+                const uint32_t bo0 = a.bloom_off[B], bo1 = a.bloom_off[B + 1];
+                const uint64_t ib = a.inc_off[t], ie = a.inc_off[t + 1];
+                if (st == round && t < e) continue;  // twin in S with smaller id owns the pair
+                a.pair_alive[p] = 0;
+                if (atomicAdd(&C[B], 1u) == 0u) {
+                    const uint32_t span = bo1 - bo0;
+                    const uint32_t nseg = (span + kSeg - 1) / kSeg;
+                    const uint32_t base = atomicAdd(&ctl->n_bseg[c3], nseg);
+                    for (uint32_t s = 0; s < nseg; ++s) {
+                        const uint32_t left = span - s * kSeg;
+                        a.bseg[c3][base + s] =
+                            make_uint4(B, bo0 + s * kSeg, left < kSeg ? left : kSeg, s == 0 ? 1u : 0u);
+                    }
+                }
+                if (st != round && bkB > 1u) {
+                    decrement(a, t, (long long)bkB - 1, L, np, round + 1, true, ib, ie);
                     ++upd;
                 }
             }
         }
+        if (!grid_barrier(ctl, bar_no)) break;
+
+        // ---------------- bloom phase
+        if (gtid == 0) {
+            ctl->n_items[par] = 0;
+            ctl->n_edges[par] = 0;
+        }
+        {
+            const uint32_t n_bseg = ldcg_ui(&ctl->n_bseg[c3]);
+            for (uint32_t i = gwarp; i < n_bseg; i += nwarps) {
+                const uint4 it = __ldcg(&a.bseg[c3][i]);
+                const uint32_t B = it.x;
+                const uint32_t c = ldcg_u32(&C[B]);
+                if (it.w && lane == 0) a.bk[B] = ldcg_u32(&a.bk[B]) - c;
+                if (lane == 0) slots += it.z;
+                if ((uint32_t)lane >= it.z) continue;
+                const uint32_t p = it.y + lane;
+                const uint8_t alive = ldcg_u8(&a.pair_alive[p]);
+                const uint2 pr = a.pairs[p];
+                if (!alive) continue;
+                decrement(a, pr.x, c, L, np, round + 1, false, 0, 0);
+                decrement(a, pr.y, c, L, np, round + 1, false, 0, 0);
+                upd += 2;
+            }
+            // clear C of the blooms the previous round touched (threads from
+            // the top of the grid, away from the bloom items above)
+            const uint32_t cp = (c3 + 2u) % 3u;
+            const uint32_t nprev = ldcg_ui(&ctl->n_bseg[cp]);
+            for (uint32_t i = nthreads - 1u - gtid; i < nprev; i += nthreads) {
+                const uint4 it = __ldcg(&a.bseg[cp][i]);
+                if (it.w) a.Cb[cp][it.x] = 0;
+            }
+        }
+        if (!grid_barrier(ctl, bar_no)) break;
+        remaining -= n_edges;
+        ++round;
+        level_jump = remaining > 0 && ldcg_ui(&ctl->n_items[np]) == 0;
     }
     upd = dev::warp_sum(upd);
-    if (lane == 0 && upd) atomicAdd(&ctrl->updates, upd);
+    if (lane == 0 && upd) atomicAdd(&ctl->updates, upd);
+    if (lane == 0 && slots) atomicAdd(&ctl->slots, slots);
+    if (gtid == 0) {
+        ctl->rounds = round;
+        ctl->kfinal = (unsigned long long)L.k;
+    }
 }
 
-// Warp per touched bloom.
-__global__ void k_bloom(const uint32_t *__restrict__ touched, const uint32_t *__restrict__ bloom_off, const uint2 *__restrict__ pairs,
-                        const uint8_t *__restrict__ pair_alive, uint32_t *bk, uint32_t *C,
-                        long long *sup, uint32_t *state, uint32_t *S_next, uint32_t round,
-                        long long k, Ctrl *ctrl) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t nt = *(volatile uint32_t *)&ctrl->n_touched;
-    unsigned long long upd = 0;
-    for (uint32_t i = warp; i < nt; i += nwarps) {
-        const uint32_t B = touched[i];
-        const uint32_t c = C[B];
-        const uint32_t b = bloom_off[B], end = bloom_off[B + 1];
-        for (uint32_t p = b + lane; p < end; p += 32) {
-            if (!pair_alive[p]) continue;
-            const uint2 pr = pairs[p];
-            decrement(sup, state, S_next, ctrl, pr.x, c, k, round);
-            decrement(sup, state, S_next, ctrl, pr.y, c, k, round);
-            upd += 2;
-        }
-        if (lane == 0) {
-            bk[B] -= c;
-            C[B] = 0;
-        }
+__global__ void k_peel_init(const uint64_t *support, uint64_t m, long long *sup, uint32_t *state,
+                            uint32_t *alive) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        sup[i] = (long long)support[i];
+        state[i] = kAlive;
+        alive[i] = (uint32_t)i;
     }
-    upd = dev::warp_sum(upd);
-    if (lane == 0 && upd) atomicAdd(&ctrl->updates, upd);
 }
 
 inline unsigned grid_for(uint64_t items, int threads, unsigned cap) {
@@ -164,95 +432,82 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     const uint64_t m = ix.m;
     res = PeelResult{};
     if (m == 0) return cudaSuccess;
-    long long *sup = al.get<long long>(m);
-    uint32_t *state = al.get<uint32_t>(m);
-    uint32_t *S = al.get<uint32_t>(m);
-    uint32_t *S_next = al.get<uint32_t>(m);
-    uint8_t *pair_alive = al.get<uint8_t>(ix.w2);
-    uint32_t *bk = al.get<uint32_t>(ix.nb);
-    uint32_t *C = al.get<uint32_t>(ix.nb);
-    uint32_t *touched = al.get<uint32_t>(ix.nb);
-    Ctrl *ctrl = al.get<Ctrl>(1);
+    const uint64_t item_cap = m + (2 * ix.w2) / kSeg + 2;
+    const uint64_t bseg_cap = ix.nb + ix.w2 / kSeg + 2;
+    PeelArgs a{};
+    a.m = m;
+    a.inc_off = ix.inc_off;
+    a.inc = ix.inc;
+    a.pairs = ix.pairs;
+    a.pair_bloom = ix.pair_bloom;
+    a.bloom_off = ix.bloom_off;
+    a.phi = phi_out;
+    a.sup = al.get<long long>(m);
+    a.state = al.get<uint32_t>(m);
+    a.pair_alive = al.get<uint8_t>(ix.w2);
+    a.bk = al.get<uint32_t>(ix.nb);
+    for (int i = 0; i < 3; ++i) {
+        a.Cb[i] = al.get<uint32_t>(ix.nb);
+        a.bseg[i] = al.get<uint4>(bseg_cap);
+    }
+    for (int i = 0; i < 2; ++i) {
+        a.items[i] = al.get<uint4>(item_cap);
+        a.alive[i] = al.get<uint32_t>(m);
+        a.near[i] = al.get<uint32_t>(m);
+    }
+    a.item_cap = item_cap;
+    a.ctl = al.get<Ctl>(1);
+    a.round_limit = m + 1;
     if (al.err != cudaSuccess) return al.err;
     cudaStream_t st = al.stream;
     al.mark(kPhPeel, false);
-    const unsigned cap = (unsigned)num_sms * 16;
-    k_peel_init<<<grid_for(m, 256, cap), 256, 0, st>>>(support, m, sup, state);
+    k_peel_init<<<grid_for(m, 256, (unsigned)num_sms * 16), 256, 0, st>>>(support, m, a.sup, a.state,
+                                                                          a.alive[0]);
     al.launches++;
-    BT_CUDA(cudaMemsetAsync(pair_alive, 1, ix.w2 ? ix.w2 : 1, st));
+    BT_CUDA(cudaMemsetAsync(a.pair_alive, 1, ix.w2 ? ix.w2 : 1, st));
     if (ix.nb) {
-        BT_CUDA(cudaMemcpyAsync(bk, ix.bloom_k, sizeof(uint32_t) * ix.nb, cudaMemcpyDeviceToDevice, st));
-        BT_CUDA(cudaMemsetAsync(C, 0, sizeof(uint32_t) * ix.nb, st));
+        BT_CUDA(cudaMemcpyAsync(a.bk, ix.bloom_k, sizeof(uint32_t) * ix.nb, cudaMemcpyDeviceToDevice, st));
+        for (int i = 0; i < 3; ++i)
+            BT_CUDA(cudaMemsetAsync(a.Cb[i], 0, sizeof(uint32_t) * ix.nb, st));
     }
-    BT_CUDA(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
-    Ctrl h{};
-    uint64_t remaining = m;
-    uint32_t nS = 0;
-    long long k = 0;
-    uint32_t round = 0;
-    const uint64_t round_limit = m + 1;
-    while (remaining > 0) {
-        if (nS == 0) {
-            unsigned long long init = ~0ull;
-            BT_CUDA(cudaMemcpyAsync(&ctrl->minsup, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-            BT_CUDA(cudaMemsetAsync(&ctrl->n_collect, 0, sizeof(uint32_t), st));
-            k_min_alive<<<grid_for(m, 256, cap), 256, 0, st>>>(state, sup, m, ctrl);
-            al.launches++;
-            BT_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-            BT_CUDA(cudaStreamSynchronize(st));
-            if (h.minsup == ~0ull) break;  // no alive edge left (cannot happen while remaining > 0)
-            long long mn = (long long)h.minsup;
-            if (mn > k) k = mn;
-            if ((unsigned long long)k > 0xFFFFFFFFull) {
-                res.status = BT_ERR_OVERFLOW;
-                break;
-            }
-            k_collect<<<grid_for(m, 256, cap), 256, 0, st>>>(state, sup, m, k, round, S, ctrl);
-            al.launches++;
-            BT_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-            BT_CUDA(cudaStreamSynchronize(st));
-            nS = h.n_collect;
-            ++res.levels;
-            if (nS == 0) {
-                res.status = BT_ERR_NOCONVERGE;
-                break;
-            }
-        }
-        BT_CUDA(cudaMemsetAsync(&ctrl->n_next, 0, 2 * sizeof(uint32_t), st));  // n_next, n_touched
-        k_incidence<<<grid_for((uint64_t)nS * 32, 256, cap), 256, 0, st>>>(
-            S, nS, round, k, ix.inc_off, ix.inc, ix.pairs, ix.pair_bloom, pair_alive, bk, C,
-            touched, sup, state, S_next, phi_out, ctrl);
-        al.launches++;
-        k_bloom<<<cap, 256, 0, st>>>(touched, ix.bloom_off, ix.pairs, pair_alive, bk, C, sup,
-                                     state, S_next, round, k, ctrl);
-        al.launches++;
-        BT_CUDA(cudaGetLastError());
-        BT_CUDA(cudaMemcpyAsync(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-        BT_CUDA(cudaStreamSynchronize(st));
-        remaining -= nS;
-        uint32_t *t = S;
-        S = S_next;
-        S_next = t;
-        nS = h.n_next;
-        ++round;
-        if (round > round_limit) {
-            res.status = BT_ERR_NOCONVERGE;
-            break;
-        }
-    }
+    Ctl h{};
+    h.n_alive[0] = (unsigned int)m;
+    h.minsup = ~0ull;
+    h.minsup2 = ~0ull;
+    BT_CUDA(cudaMemcpyAsync(a.ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    int bps = 0;
+    BT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_peel, kPeelThreads, 0));
+    if (bps < 1) return cudaErrorCooperativeLaunchTooLarge;
+    dim3 grid((unsigned)(num_sms * bps)), block(kPeelThreads);
+    void *kargs[] = {&a};
+    BT_CUDA(cudaLaunchCooperativeKernel((void *)k_peel, grid, block, kargs, 0, st));
+    al.launches++;
+    BT_CUDA(cudaMemcpyAsync(&h, a.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    BT_CUDA(cudaStreamSynchronize(st));
     al.mark(kPhPeel, true);
-    res.rounds = round;
+    if (h.err & kErrBarrier) res.status = BT_ERR_CUDA;
+    else if (h.err & kErrPeelOverflow) res.status = BT_ERR_OVERFLOW;
+    else if (h.err & kErrRounds) res.status = BT_ERR_NOCONVERGE;
+    res.rounds = h.rounds;
+    res.levels = h.levels;
+    res.windows = h.windows;
     res.updates = h.updates;
-    res.kmax = (uint64_t)k;
-    al.put(sup);
-    al.put(state);
-    al.put(S);
-    al.put(S_next);
-    al.put(pair_alive);
-    al.put(bk);
-    al.put(C);
-    al.put(touched);
-    al.put(ctrl);
+    res.slots = h.slots;
+    res.kmax = h.kfinal;
+    al.put(a.sup);
+    al.put(a.state);
+    al.put(a.pair_alive);
+    al.put(a.bk);
+    for (int i = 0; i < 3; ++i) {
+        al.put(a.Cb[i]);
+        al.put(a.bseg[i]);
+    }
+    for (int i = 0; i < 2; ++i) {
+        al.put(a.items[i]);
+        al.put(a.alive[i]);
+        al.put(a.near[i]);
+    }
+    al.put(a.ctl);
     return cudaSuccess;
 }
 
