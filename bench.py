@@ -34,6 +34,7 @@ WORKLOADS = {
                    gammaL=2.4, cap=20000, seed=2),
     "small": dict(name="chunglu-2k-1.5k-20k", nU=2000, nL=1500, m=20000, gammaU=2.2, gammaL=2.5,
                   cap=0, seed=1),
+    "batch": dict(name="batch-4096-chunglu-logU(100,200000)", graphs=4096),
 }
 WORKLOAD = WORKLOADS["medium"]
 METRIC = "edges decomposed/s"
@@ -198,6 +199,64 @@ def cpu_baseline():
             "seconds": dt}
 
 
+def gen_batch(n):
+    import concurrent.futures as cf
+
+    from paper_2001_06111_gb300 import synth
+    with cf.ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 4)) as ex:
+        return list(ex.map(synth.batch_graph, range(n)))
+
+
+def run_batch(args):
+    """4,096 independent graphs: one bt_decompose per graph (plain path) vs one
+    bt_decompose_batch over all of them, both through the C ABI with host
+    buffers; results must be identical graph by graph."""
+    import torch
+    from paper_2001_06111_gb300 import bitruss as bt
+    from paper_2001_06111_gb300 import build
+
+    build.build()
+    n = WORKLOAD["graphs"]
+    t0 = time.perf_counter()
+    graphs = gen_batch(n)
+    gen_s = time.perf_counter() - t0
+    m_total = sum(g.m for g in graphs)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    h = bt.bt_create(0, stream)
+    gs = [(g.edges, g.nU, g.nL) for g in graphs]
+    for _ in range(1):  # warm-up (memory pool, module load)
+        bt.bt_decompose_batch(h, gs[:64])
+        for e, nU, nL in gs[:64]:
+            bt.bt_decompose(h, e, nU, nL)
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outs, st = bt.bt_decompose_batch(h, gs)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plain = [bt.bt_decompose(h, e, nU, nL)[:2] for e, nU, nL in gs]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    clk = clocks.stop()
+    exact = all(np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) for a, b in zip(outs, plain))
+    line = {
+        "metric": "batched graphs/s", "value": n / t_batch, "unit": "graphs/s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "graphs": n, "edges": m_total,
+                   "generation_s": gen_s, "parallelism": "replicas x1"},
+        "plain": {"value": n / t_plain, "unit": "graphs/s", "ms": t_plain * 1e3},
+        "speedup_vs_plain": t_plain / t_batch, "bit_exact_vs_plain": bool(exact),
+        "batch_stats": st, "edges_per_s": m_total / t_batch, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0 if exact else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,6 +273,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
 
     ws, rank, local = dist_env()
     # the CPU baseline runs before the first CUDA call (rank 0, N=1 only)

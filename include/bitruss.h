@@ -205,6 +205,48 @@ int bt_profile_read(const bt_handle *h, bt_profile *out);
 int bt_count_support_static(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL,
                             uint64_t *d_support_out, uint32_t flags, void *cuda_stream);
 
+/* One graph of a batch (bt_decompose_batch).  Pointers are host pointers,
+ * or device pointers when the batch call passes BT_DEVICE_PTRS. */
+typedef struct {
+    const int32_t *edges;   /* int32 pairs (u, v), 2*m values, as for bt_decompose */
+    uint64_t m;
+    uint32_t nU, nL;
+    uint64_t *support_out;  /* uint64[m] or NULL */
+    uint32_t *phi_out;      /* uint32[m] */
+} bt_graph;
+
+/* Batch schedule.  Zero fields are chosen by the library. */
+typedef struct {
+    uint64_t max_edges_per_launch;  /* graphs are packed into unions of at most this many edges */
+    uint32_t reserved[4];
+} bt_tune;
+
+typedef struct {
+    uint64_t graphs;           /* graphs decomposed */
+    uint64_t launches;         /* union graphs (device pipelines) used */
+    uint64_t edges;            /* total edges */
+    uint64_t wedges;           /* total priority-obeyed wedges */
+    uint64_t rounds, levels;   /* peeling rounds and levels, summed over unions */
+    uint64_t support_updates;
+} bt_batch_stats;
+
+/*
+ * Bitruss decomposition of n independent graphs.  Butterflies never span two
+ * graphs, so the decomposition of their disjoint union is the union of their
+ * decompositions (Defs. 4-5): the graphs are relabelled on the device into
+ * one union (upper and lower ids shifted per graph, keeping every graph's own
+ * priority order, Def. 7) and decomposed by one pipeline -- one count, one
+ * index emit and one persistent peeling launch -- so the peel's rounds are
+ * shared by all graphs instead of paid per graph.  Results are exactly those
+ * of bt_decompose on each graph alone.  Graphs are packed into unions of at
+ * most tune->max_edges_per_launch edges (0: as many as device memory allows;
+ * a union that does not fit is split in two and retried).
+ * stats may be NULL; tune may be NULL.
+ * Errors: as bt_decompose; BT_ERR_RANGE names the first graph with a bad id.
+ */
+int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const bt_tune *tune,
+                       bt_batch_stats *stats, uint32_t flags);
+
 /*
  * Device bytes a bt_decompose of this graph needs (host computation, O(m)
  * time; edges are host pointers).  It counts priority-obeyed wedges exactly,

@@ -32,7 +32,7 @@ BT_TIE_LOWER_FIRST = 0x2
 
 EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_build_index",
             "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
-            "bt_profile_read", "bt_count_support_static")
+            "bt_profile_read", "bt_count_support_static", "bt_decompose_batch")
 
 
 class BitrussError(RuntimeError):
@@ -67,6 +67,23 @@ class Profile(ctypes.Structure):
                 ("rounds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
                 ("support_updates", ctypes.c_uint64), ("pair_slots", ctypes.c_uint64),
                 ("link_visits", ctypes.c_uint64)]
+
+
+class Graph(ctypes.Structure):
+    _fields_ = [("edges", ctypes.c_void_p), ("m", ctypes.c_uint64), ("nU", ctypes.c_uint32),
+                ("nL", ctypes.c_uint32), ("support_out", ctypes.c_void_p),
+                ("phi_out", ctypes.c_void_p)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("max_edges_per_launch", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 4)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("graphs", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("edges", ctypes.c_uint64), ("wedges", ctypes.c_uint64),
+                ("rounds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
+                ("support_updates", ctypes.c_uint64)]
 
 
 def _as_dict(s: ctypes.Structure) -> dict:
@@ -105,6 +122,8 @@ def load(path: str = LIB_PATH):
         lib.bt_index_export.argtypes = [P, P, P, P]
         lib.bt_decompose.argtypes = [P, P, U64, U32, U32, P, P, ctypes.POINTER(PeelStats), U32]
         lib.bt_count_support_static.argtypes = [P, U64, U32, U32, P, U32, P]
+        lib.bt_decompose_batch.argtypes = [P, ctypes.POINTER(Graph), U32, ctypes.POINTER(Tune),
+                                           ctypes.POINTER(BatchStats), U32]
         lib.bt_profile_enable.argtypes = [P, I]
         lib.bt_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         lib.bt_estimate_bytes.argtypes = [P, U64, U32, U32, U32, ctypes.POINTER(U64),
@@ -243,6 +262,32 @@ def bt_count_support_static(d_edges, nU: int, nL: int, d_support_out, flags: int
                                         flags, s)
     if rc != BT_OK:
         raise BitrussError(rc, "bt_count_support_static failed")
+
+
+def bt_decompose_batch(h: Handle, graphs, flags: int = 0, max_edges_per_launch: int = 0,
+                       want_support: bool = True):
+    """Decompose a list of graphs, each given as (edges, nU, nL) with numpy
+    (host) or CUDA torch (device) edge lists; returns ([(support, phi)], stats)."""
+    n = len(graphs)
+    arr = (Graph * max(n, 1))()
+    keep, outs = [], []
+    dev_flag = 0
+    for i, (edges, nU, nL) in enumerate(graphs):
+        ptr, m, f, k = _edges_arg(edges)
+        dev_flag |= f
+        keep.append(k)
+        dev = k if f & BT_DEVICE_PTRS else None
+        sup, sptr = (None, None)
+        if want_support:
+            sup, sptr = _out(dev, m, np.uint64, _torch_dtype("uint64"), None)
+        phi, pptr = _out(dev, m, np.uint32, _torch_dtype("uint32"), None)
+        arr[i] = Graph(ptr, m, nU, nL, sptr, pptr)
+        outs.append((sup, phi))
+    tune = Tune(max_edges_per_launch)
+    st = BatchStats()
+    _check(h, load().bt_decompose_batch(h.ptr, arr, n, ctypes.byref(tune), ctypes.byref(st),
+                                        flags | dev_flag))
+    return outs, _as_dict(st)
 
 
 def bt_profile_enable(h: Handle, on: bool = True):

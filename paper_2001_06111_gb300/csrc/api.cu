@@ -450,6 +450,163 @@ int bt_profile_read(const bt_handle *h, bt_profile *out) {
     return BT_OK;
 }
 
+// Decomposes graphs[0..n) as one disjoint union (see bt_decompose_batch).
+static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uint32_t flags,
+                           bt_batch_stats *acc, bt::Alloc &al) {
+    const bool dev = flags & BT_DEVICE_PTRS;
+    std::vector<uint64_t> goff(n + 1, 0);
+    std::vector<uint32_t> offU(n), offL(n), gnU(n), gnL(n);
+    uint64_t NU = 0, NL = 0;
+    for (uint32_t g = 0; g < n; ++g) {
+        goff[g + 1] = goff[g] + graphs[g].m;
+        offU[g] = (uint32_t)NU;
+        offL[g] = (uint32_t)NL;
+        gnU[g] = graphs[g].nU;
+        gnL[g] = graphs[g].nL;
+        NU += graphs[g].nU;
+        NL += graphs[g].nL;
+    }
+    const uint64_t M = goff[n];
+    if (NU + NL >= 0xFFFFFFFFull || M >= (1ull << 31))
+        return fail(h, BT_ERR_ARG, "union of %u graphs exceeds 2^31 edges or 2^32 vertices", n);
+    al.err = cudaSuccess;
+    int rc = BT_OK;
+    int32_t *d_edges = al.get<int32_t>(2 * M);
+    uint64_t *d_goff = al.get<uint64_t>(n + 1);
+    uint32_t *d_tab = al.get<uint32_t>(4 * (size_t)n + 1);
+    uint64_t *d_sup = al.get<uint64_t>(M);
+    uint32_t *d_phi = al.get<uint32_t>(M);
+    if (al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating the batch union");
+    cudaError_t e = cudaSuccess;
+    if (rc == BT_OK) {
+        std::vector<uint32_t> tab(4 * (size_t)n + 1);
+        std::copy(offU.begin(), offU.end(), tab.begin());
+        std::copy(offL.begin(), offL.end(), tab.begin() + n);
+        std::copy(gnU.begin(), gnU.end(), tab.begin() + 2 * (size_t)n);
+        std::copy(gnL.begin(), gnL.end(), tab.begin() + 3 * (size_t)n);
+        tab[4 * (size_t)n] = 0xFFFFFFFFu;  // lowest failing graph
+        e = cudaMemcpyAsync(d_goff, goff.data(), 8 * (n + 1), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_tab, tab.data(), 4 * tab.size(), cudaMemcpyHostToDevice, h->stream);
+        for (uint32_t g = 0; g < n && e == cudaSuccess; ++g)
+            if (graphs[g].m)
+                e = cudaMemcpyAsync(d_edges + 2 * goff[g], graphs[g].edges, 8 * graphs[g].m,
+                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->err_word, 0, sizeof(uint32_t), h->stream);
+        uint32_t *bad = d_tab + 4 * (size_t)n;
+        if (e == cudaSuccess)
+            e = bt::union_edges(d_edges, M, d_goff, n, d_tab, d_tab + n, d_tab + 2 * (size_t)n,
+                                d_tab + 3 * (size_t)n, h->err_word, bad, al);
+        uint32_t hw[2] = {0, 0};
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&hw[0], h->err_word, 4, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hw[1], bad, 4, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "staging the batch");
+        else if (hw[0] & bt::kErrRange)
+            rc = fail(h, BT_ERR_RANGE, "graph %u of the batch has a vertex id outside its layers", hw[1]);
+    }
+    if (rc == BT_OK && M > 0)
+        rc = build_index_impl(h, d_edges, M, (uint32_t)NU, (uint32_t)NL,
+                              (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, d_sup, al);
+    bt::PeelResult pr;
+    if (rc == BT_OK && M > 0) {
+        e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
+        else if (pr.status == BT_ERR_OVERFLOW)
+            rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
+        else if (pr.status != BT_OK)
+            rc = fail(h, pr.status, "peeling stopped: device barrier timeout or round limit");
+    }
+    if (rc == BT_OK) {
+        for (uint32_t g = 0; g < n && e == cudaSuccess; ++g) {
+            if (!graphs[g].m) continue;
+            if (graphs[g].support_out)
+                e = deliver(h, graphs[g].support_out, d_sup + goff[g], 8 * graphs[g].m, flags);
+            if (e == cudaSuccess)
+                e = deliver(h, graphs[g].phi_out, d_phi + goff[g], 4 * graphs[g].m, flags);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "returning batch results");
+    }
+    if (rc == BT_OK && acc) {
+        acc->graphs += n;
+        acc->launches += 1;
+        acc->edges += M;
+        acc->wedges += h->index.w;
+        acc->rounds += pr.rounds;
+        acc->levels += pr.levels;
+        acc->support_updates += pr.updates;
+    }
+    al.put(d_edges);
+    al.put(d_goff);
+    al.put(d_tab);
+    al.put(d_sup);
+    al.put(d_phi);
+    cudaStreamSynchronize(h->stream);
+    return rc;
+}
+
+// Packs graphs into unions of at most `cap` edges; a union that runs out of
+// device memory is split in two and retried.
+static int decompose_packed(bt_handle *h, const bt_graph *graphs, uint32_t n, uint64_t cap,
+                            uint32_t flags, bt_batch_stats *acc, bt::Alloc &al) {
+    uint32_t g0 = 0;
+    while (g0 < n) {
+        uint32_t g1 = g0;
+        uint64_t edges = 0, verts = 0;
+        while (g1 < n && (g1 == g0 || (edges + graphs[g1].m <= cap &&
+                                      verts + graphs[g1].nU + graphs[g1].nL < 0xF0000000ull))) {
+            edges += graphs[g1].m;
+            verts += (uint64_t)graphs[g1].nU + graphs[g1].nL;
+            ++g1;
+        }
+        int rc = decompose_union(h, graphs + g0, g1 - g0, flags, acc, al);
+        if (rc == BT_ERR_NOMEM && g1 - g0 > 1) {
+            uint32_t half = (g1 - g0) / 2;
+            rc = decompose_packed(h, graphs + g0, half, cap, flags, acc, al);
+            if (rc == BT_OK)
+                rc = decompose_packed(h, graphs + g0 + half, g1 - g0 - half, cap, flags, acc, al);
+        }
+        if (rc != BT_OK) return rc;
+        g0 = g1;
+    }
+    return BT_OK;
+}
+
+int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const bt_tune *tune,
+                       bt_batch_stats *stats, uint32_t flags) {
+    if (!h) return BT_ERR_ARG;
+    h->err.clear();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (flags & ~(BT_DEVICE_PTRS | BT_TIE_LOWER_FIRST))
+        return fail(h, BT_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if (n && !graphs) return fail(h, BT_ERR_ARG, "graphs is NULL");
+    for (uint32_t g = 0; g < n; ++g) {
+        const bt_graph &G = graphs[g];
+        if (G.m && (!G.edges || !G.phi_out)) return fail(h, BT_ERR_ARG, "graph %u: NULL edges or phi_out", g);
+        if (G.m >= (1ull << 31)) return fail(h, BT_ERR_ARG, "graph %u: m exceeds 2^31 - 1", g);
+        if (G.m > (uint64_t)G.nU * G.nL)
+            return fail(h, BT_ERR_DUP, "graph %u: m exceeds nU * nL", g);
+    }
+    uint64_t cap = (tune && tune->max_edges_per_launch) ? tune->max_edges_per_launch : (1ull << 31) - 1;
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    call_begin(h, al, 0, 0);
+    bt_batch_stats acc{};
+    int rc = decompose_packed(h, graphs, n, cap, flags, &acc, al);
+    call_end(h, al);
+    if (rc == BT_OK) {
+        h->last.n_edges = acc.edges;
+        h->last.n_wedges = acc.wedges;
+        h->last.rounds = acc.rounds;
+        h->last.levels = acc.levels;
+        h->last.support_updates = acc.support_updates;
+    }
+    if (stats && rc == BT_OK) *stats = acc;
+    return rc;
+}
+
 int bt_estimate_bytes(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
                       uint64_t *bytes_out, uint64_t *wedges_out) {
     if (!bytes_out || (m && !edges)) return BT_ERR_ARG;

@@ -103,6 +103,12 @@ struct Csr {
 cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
                       Csr &g, uint32_t *err_word, Alloc &al);
 void free_csr(Csr &g, Alloc &al);
+// In-place relabelling of ng concatenated edge lists (graph g owns edges
+// [goff[g], goff[g+1])) into one disjoint union; range errors set kErrRange
+// and the lowest failing graph index in *bad_graph.
+cudaError_t union_edges(int32_t *d_edges, uint64_t m_total, const uint64_t *d_goff, uint32_t ng,
+                        const uint32_t *d_offU, const uint32_t *d_offL, const uint32_t *d_nU,
+                        const uint32_t *d_nL, uint32_t *err_word, uint32_t *bad_graph, Alloc &al);
 
 // ---------------------------------------------------------------- counting
 struct CountOut {

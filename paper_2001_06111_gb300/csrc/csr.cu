@@ -127,7 +127,44 @@ inline unsigned grid_for(uint64_t items, int threads, unsigned cap = 152 * 32) {
     return (unsigned)(g < cap ? g : cap);
 }
 
+// Relabels a concatenation of independent graphs into one disjoint union:
+// edge i of graph g gets its upper id shifted by offU[g] and its lower id by
+// offL[g].  Ids are checked against the graph's own layer sizes first; the
+// lowest failing graph index is kept in *bad_graph.
+__global__ void k_union(int32_t *edges, uint64_t m_total, const uint64_t *goff, uint32_t ng,
+                        const uint32_t *offU, const uint32_t *offL, const uint32_t *gnU,
+                        const uint32_t *gnL, uint32_t *err, uint32_t *bad_graph) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m_total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = ng;  // largest g with goff[g] <= i
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (goff[mid] <= i) lo = mid; else hi = mid;
+        }
+        const uint32_t g = lo;
+        int2 e = reinterpret_cast<int2 *>(edges)[i];
+        if (e.x < 0 || e.y < 0 || (uint32_t)e.x >= gnU[g] || (uint32_t)e.y >= gnL[g]) {
+            atomicOr(err, kErrRange);
+            atomicMin(bad_graph, g);
+            continue;
+        }
+        e.x += (int32_t)offU[g];
+        e.y += (int32_t)offL[g];
+        reinterpret_cast<int2 *>(edges)[i] = e;
+    }
+}
+
 }  // namespace
+
+cudaError_t union_edges(int32_t *d_edges, uint64_t m_total, const uint64_t *d_goff, uint32_t ng,
+                        const uint32_t *d_offU, const uint32_t *d_offL, const uint32_t *d_nU,
+                        const uint32_t *d_nL, uint32_t *err_word, uint32_t *bad_graph, Alloc &al) {
+    if (m_total == 0) return cudaSuccess;
+    k_union<<<grid_for(m_total, 256), 256, 0, al.stream>>>(d_edges, m_total, d_goff, ng, d_offU,
+                                                           d_offL, d_nU, d_nL, err_word, bad_graph);
+    al.launches++;
+    return cudaGetLastError();
+}
 
 cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
                       Csr &g, uint32_t *err_word, Alloc &al) {
