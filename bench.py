@@ -225,6 +225,7 @@ def run_batch(args):
     torch.cuda.set_stream(stream)
     h = bt.bt_create(0, stream)
     gs = [(g.edges, g.nU, g.nL) for g in graphs]
+    bt.bt_profile_enable(h, True)
     for _ in range(1):  # warm-up (memory pool, module load)
         bt.bt_decompose_batch(h, gs[:64])
         for e, nU, nL in gs[:64]:
@@ -236,6 +237,7 @@ def run_batch(args):
     outs, st = bt.bt_decompose_batch(h, gs)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
+    prof = bt.bt_profile_read(h)
     t0 = time.perf_counter()
     plain = [bt.bt_decompose(h, e, nU, nL)[:2] for e, nU, nL in gs]
     torch.cuda.synchronize()
@@ -251,6 +253,8 @@ def run_batch(args):
         "plain": {"value": n / t_plain, "unit": "graphs/s", "ms": t_plain * 1e3},
         "speedup_vs_plain": t_plain / t_batch, "bit_exact_vs_plain": bool(exact),
         "batch_stats": st, "edges_per_s": m_total / t_batch, "clocks": clk,
+        "phases_ms": {k: prof[k] for k in ("csr_ms", "count_ms", "emit_ms", "peel_ms", "total_ms")},
+        "gpu_launches": prof["launches"],
     }
     print(json.dumps(line), flush=True)
     h.close()

@@ -26,9 +26,13 @@
 // every block returns.  Work is split into items of at most kSeg entries: an
 // edge of S with a long link list becomes several incidence items, and a
 // touched bloom with many pairs several bloom items, so no warp straggles on
-// a hub.  Counters and work lists are double-buffered by round parity, which
-// leaves two barriers per round.  Data written by other blocks during the
-// kernel is read with L2 (.cg) loads.
+// a hub.  A twin pair carries the round it died in; the edges of S race to
+// stamp it with atomicCAS, so exactly one of them counts it in C(B) (the
+// twin rule above, without reading the twin's state), and the twin
+// decrements are applied by the bloom phase, which sees which pairs died in
+// this round.  Counters and work lists are double- or triple-buffered by
+// round, which leaves two barriers per round.  Data written by other blocks
+// during the kernel is read with L2 (.cg) loads.
 #include "bt_device.cuh"
 #include "bt_internal.cuh"
 
@@ -72,11 +76,11 @@ struct PeelArgs {
     long long *sup;
     uint32_t *state;
     uint32_t *phi;
-    uint8_t *pair_alive;
+    uint32_t *died;    // round a twin pair died in (kAlive while alive)
     uint32_t *bk;
     uint32_t *Cb[3];
     uint4 *items[2];   // (edge, first link lo, first link hi, count | head flag << 31)
-    uint4 *bseg[3];    // (bloom, first pair, count, head flag)
+    uint4 *bseg[3];    // (bloom, first pair, count | head flag << 31, bloom number at round start)
     uint32_t *alive[2];
     uint32_t *near[2];
     uint64_t item_cap;
@@ -101,11 +105,6 @@ __device__ __forceinline__ unsigned long long now_ns() {
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned int ldcg_ui(const unsigned int *p) { return __ldcg(p); }
 __device__ __forceinline__ long long ldcg_ll(const long long *p) { return __ldcg(p); }
-__device__ __forceinline__ uint8_t ldcg_u8(const uint8_t *p) {
-    unsigned short v;
-    asm volatile("ld.global.cg.u8 %0, [%1];" : "=h"(v) : "l"(p));
-    return (uint8_t)v;
-}
 
 // Grid-wide barrier over all blocks of a cooperative launch.  Arrivals go
 // to one monotonic counter (release); barrier number b completes when the
@@ -154,8 +153,9 @@ __device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no) {
 // Queue edge e (links [ib, ie)) for the round `next_round`: one incidence
 // item per kSeg links, each carrying its link range.
 __device__ __forceinline__ void push_edge(const PeelArgs &a, uint32_t e, uint32_t dst,
-                                          uint32_t next_round, uint64_t ib, uint64_t ie) {
+                                          uint32_t next_round, uint64_t ib, uint64_t ie, long long k) {
     a.state[e] = next_round;
+    a.phi[e] = (uint32_t)k;  // e leaves in a batch of this level
     const uint64_t d = ie - ib;
     const uint32_t nseg = d == 0 ? 1u : (uint32_t)((d + kSeg - 1) / kSeg);
     const uint32_t base = atomicAdd(&a.ctl->n_items[dst], nseg);
@@ -186,7 +186,7 @@ __device__ __forceinline__ void decrement(const PeelArgs &a, uint32_t e, long lo
             ib = a.inc_off[e];
             ie = a.inc_off[e + 1];
         }
-        push_edge(a, e, dst, next_round, ib, ie);
+        push_edge(a, e, dst, next_round, ib, ie, L.k);
     }
     if (old >= L.khi && now < L.khi) push_near(a, e, L.nq);
 }
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             for (uint32_t i = gtid; i < nn2; i += nthreads) {
                 const uint32_t e = ldcg_u32(&a.near[L.nq][i]);
                 if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k)
-                    push_edge(a, e, par, round, a.inc_off[e], a.inc_off[e + 1]);
+                    push_edge(a, e, par, round, a.inc_off[e], a.inc_off[e + 1], L.k);
             }
             if (gtid == 0) atomicAdd(&ctl->levels, 1ull);
             if (!grid_barrier(ctl, bar_no)) break;
@@ -329,36 +329,25 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             if (gtid == 0) ctl->n_bseg[(c3 + 1u) % 3u] = 0;
             for (uint32_t i = gwarp; i < n_items; i += nwarps) {
                 const uint4 it = i == gwarp ? it0 : __ldcg(&a.items[par][i]);
-                const uint32_t e = it.x;
-                if ((it.w >> 31) && lane == 0) a.phi[e] = (uint32_t)L.k;
                 const uint32_t cnt = it.w & 0x7FFFFFFFu;
                 if ((uint32_t)lane >= cnt) continue;
                 const uint64_t j = ((uint64_t)it.z << 32 | it.y) + lane;
                 const uint32_t p = a.inc[j];
-                const uint8_t alive = ldcg_u8(&a.pair_alive[p]);
-                const uint2 pr = a.pairs[p];
                 const uint32_t B = a.pair_bloom[p];
-                if (!alive) continue;
-                const uint32_t t = pr.x == e ? pr.y : pr.x;
-                const uint32_t st = ldcg_u32(&a.state[t]);
+                // the first edge of S to stamp the pair kills it (once)
+                if (atomicCAS(&a.died[p], kAlive, round) != kAlive) continue;
                 const uint32_t bkB = ldcg_u32(&a.bk[B]);
                 const uint32_t bo0 = a.bloom_off[B], bo1 = a.bloom_off[B + 1];
-                const uint64_t ib = a.inc_off[t], ie = a.inc_off[t + 1];
-                if (st == round && t < e) continue;  // twin in S with smaller id owns the pair
-                a.pair_alive[p] = 0;
                 if (atomicAdd(&C[B], 1u) == 0u) {
                     const uint32_t span = bo1 - bo0;
                     const uint32_t nseg = (span + kSeg - 1) / kSeg;
                     const uint32_t base = atomicAdd(&ctl->n_bseg[c3], nseg);
                     for (uint32_t s = 0; s < nseg; ++s) {
                         const uint32_t left = span - s * kSeg;
-                        a.bseg[c3][base + s] =
-                            make_uint4(B, bo0 + s * kSeg, left < kSeg ? left : kSeg, s == 0 ? 1u : 0u);
+                        a.bseg[c3][base + s] = make_uint4(
+                            B, bo0 + s * kSeg, (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u),
+                            bkB);
                     }
-                }
-                if (st != round && bkB > 1u) {
-                    decrement(a, t, (long long)bkB - 1, L, np, round + 1, true, ib, ie);
-                    ++upd;
                 }
             }
         }
@@ -373,18 +362,31 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             const uint32_t n_bseg = ldcg_ui(&ctl->n_bseg[c3]);
             for (uint32_t i = gwarp; i < n_bseg; i += nwarps) {
                 const uint4 it = __ldcg(&a.bseg[c3][i]);
-                const uint32_t B = it.x;
+                const uint32_t B = it.x, kB = it.w, cnt = it.z & 0x7FFFFFFFu;
                 const uint32_t c = ldcg_u32(&C[B]);
-                if (it.w && lane == 0) a.bk[B] = ldcg_u32(&a.bk[B]) - c;
-                if (lane == 0) slots += it.z;
-                if ((uint32_t)lane >= it.z) continue;
+                if ((it.z >> 31) && lane == 0) a.bk[B] = kB - c;
+                if (lane == 0) slots += cnt;
+                if ((uint32_t)lane >= cnt) continue;
                 const uint32_t p = it.y + lane;
-                const uint8_t alive = ldcg_u8(&a.pair_alive[p]);
+                const uint32_t d = ldcg_u32(&a.died[p]);
                 const uint2 pr = a.pairs[p];
-                if (!alive) continue;
-                decrement(a, pr.x, c, L, np, round + 1, false, 0, 0);
-                decrement(a, pr.y, c, L, np, round + 1, false, 0, 0);
-                upd += 2;
+                if (d == kAlive) {
+                    // a surviving pair: one butterfly lost per dead pair
+                    decrement(a, pr.x, c, L, np, round + 1, false, 0, 0);
+                    decrement(a, pr.y, c, L, np, round + 1, false, 0, 0);
+                    upd += 2;
+                } else if (d == round && kB > 1u) {
+                    // died now: a member outside S loses its k_B - 1 butterflies
+                    const uint32_t sx = ldcg_u32(&a.state[pr.x]), sy = ldcg_u32(&a.state[pr.y]);
+                    if (sx != round) {
+                        decrement(a, pr.x, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+                        ++upd;
+                    }
+                    if (sy != round) {
+                        decrement(a, pr.y, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+                        ++upd;
+                    }
+                }
             }
             // clear C of the blooms the previous round touched (threads from
             // the top of the grid, away from the bloom items above)
@@ -444,7 +446,7 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     a.phi = phi_out;
     a.sup = al.get<long long>(m);
     a.state = al.get<uint32_t>(m);
-    a.pair_alive = al.get<uint8_t>(ix.w2);
+    a.died = al.get<uint32_t>(ix.w2);
     a.bk = al.get<uint32_t>(ix.nb);
     for (int i = 0; i < 3; ++i) {
         a.Cb[i] = al.get<uint32_t>(ix.nb);
@@ -464,7 +466,7 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     k_peel_init<<<grid_for(m, 256, (unsigned)num_sms * 16), 256, 0, st>>>(support, m, a.sup, a.state,
                                                                           a.alive[0]);
     al.launches++;
-    BT_CUDA(cudaMemsetAsync(a.pair_alive, 1, ix.w2 ? ix.w2 : 1, st));
+    BT_CUDA(cudaMemsetAsync(a.died, 0xFF, sizeof(uint32_t) * (ix.w2 ? ix.w2 : 1), st));
     if (ix.nb) {
         BT_CUDA(cudaMemcpyAsync(a.bk, ix.bloom_k, sizeof(uint32_t) * ix.nb, cudaMemcpyDeviceToDevice, st));
         for (int i = 0; i < 3; ++i)
@@ -496,7 +498,7 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     res.kmax = h.kfinal;
     al.put(a.sup);
     al.put(a.state);
-    al.put(a.pair_alive);
+    al.put(a.died);
     al.put(a.bk);
     for (int i = 0; i < 3; ++i) {
         al.put(a.Cb[i]);
