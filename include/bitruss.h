@@ -247,6 +247,56 @@ typedef struct {
 int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const bt_tune *tune,
                        bt_batch_stats *stats, uint32_t flags);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop with continuous batching.  Each submitted request is one
+ * graph (host pointers, as in bt_graph; the caller keeps edges and outputs
+ * alive until the request completes).  Worker threads, each owning a handle
+ * (stream, memory pool, device-resident BE-Index), take all waiting requests
+ * that fit the memory budget whenever they become free and decompose them as
+ * one batch (bt_decompose_batch); requests that arrive meanwhile join the next
+ * batch, and with several workers batches overlap on the device.  Admission
+ * uses an O(m) upper bound on a request's device bytes from its degrees
+ * (priority-obeyed wedges <= sum over edges of min(d(u), d(v)), Lemma 6).
+ * Results are exactly those of bt_decompose on the graph alone. */
+typedef struct bt_server bt_server;
+
+typedef struct {
+    uint64_t memory_budget_bytes;  /* admission budget; 0 = 120 GiB */
+    uint32_t workers;              /* concurrent batches; 0 = 2 */
+    uint32_t max_batch_graphs;     /* 0 = unlimited; 1 = one request at a time (plain serial) */
+    uint32_t flags;                /* 0 or BT_TIE_LOWER_FIRST */
+    uint32_t reserved;
+} bt_server_config;
+
+typedef struct {
+    int done;                /* 1 when the request completed */
+    int status;              /* its bt_status once done */
+    double queue_seconds;    /* submit -> batch start (so far, if not started) */
+    double latency_seconds;  /* submit -> completion (so far, if not done) */
+    uint64_t admitted_bytes; /* the admission bound used */
+} bt_request_info;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, batches, queued;
+    uint64_t max_batch_graphs;
+    uint64_t in_flight_bytes, peak_in_flight_bytes;
+    uint64_t edges;
+    double busy_seconds;     /* summed over workers */
+} bt_server_stats;
+
+/* Start a server on `device`.  cfg may be NULL (defaults).
+ * Errors: BT_ERR_ARG, BT_ERR_NOMEM, BT_ERR_CUDA. */
+int bt_server_create(bt_server **s, int device, const bt_server_config *cfg);
+/* Finish every queued request, then stop the workers and free the server. */
+int bt_server_destroy(bt_server *s);
+/* Queue one graph; returns its id.  Errors: BT_ERR_ARG, BT_ERR_NOMEM. */
+int bt_server_submit(bt_server *s, const bt_graph *g, uint64_t *request_id);
+/* State of a request (wait != 0 blocks until it completes).  Once a done
+ * request has been reported its id is released.  Errors: BT_ERR_ARG,
+ * BT_ERR_STATE (unknown or released id). */
+int bt_server_poll(bt_server *s, uint64_t request_id, int wait, bt_request_info *info);
+int bt_server_stats_read(bt_server *s, bt_server_stats *out);
+
 /*
  * Device bytes a bt_decompose of this graph needs (host computation, O(m)
  * time; edges are host pointers).  It counts priority-obeyed wedges exactly,

@@ -32,7 +32,9 @@ BT_TIE_LOWER_FIRST = 0x2
 
 EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_build_index",
             "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
-            "bt_profile_read", "bt_count_support_static", "bt_decompose_batch")
+            "bt_profile_read", "bt_count_support_static", "bt_decompose_batch",
+            "bt_server_create", "bt_server_destroy", "bt_server_submit", "bt_server_poll",
+            "bt_server_stats_read")
 
 
 class BitrussError(RuntimeError):
@@ -86,13 +88,33 @@ class BatchStats(ctypes.Structure):
                 ("support_updates", ctypes.c_uint64)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("workers", ctypes.c_uint32),
+                ("max_batch_graphs", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int),
+                ("queue_seconds", ctypes.c_double), ("latency_seconds", ctypes.c_double),
+                ("admitted_bytes", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("max_batch_graphs", ctypes.c_uint64),
+                ("in_flight_bytes", ctypes.c_uint64), ("peak_in_flight_bytes", ctypes.c_uint64),
+                ("edges", ctypes.c_uint64), ("busy_seconds", ctypes.c_double)]
+
+
 def _as_dict(s: ctypes.Structure) -> dict:
     out = {}
     for f, t in s._fields_:
         if f == "reserved":
             continue
         v = getattr(s, f)
-        out[f] = float(v) if t is ctypes.c_float else int(v)
+        out[f] = float(v) if t in (ctypes.c_float, ctypes.c_double) else int(v)
     return out
 
 
@@ -124,6 +146,11 @@ def load(path: str = LIB_PATH):
         lib.bt_count_support_static.argtypes = [P, U64, U32, U32, P, U32, P]
         lib.bt_decompose_batch.argtypes = [P, ctypes.POINTER(Graph), U32, ctypes.POINTER(Tune),
                                            ctypes.POINTER(BatchStats), U32]
+        lib.bt_server_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(ServerConfig)]
+        lib.bt_server_destroy.argtypes = [P]
+        lib.bt_server_submit.argtypes = [P, ctypes.POINTER(Graph), ctypes.POINTER(U64)]
+        lib.bt_server_poll.argtypes = [P, U64, I, ctypes.POINTER(RequestInfo)]
+        lib.bt_server_stats_read.argtypes = [P, ctypes.POINTER(ServerStats)]
         lib.bt_profile_enable.argtypes = [P, I]
         lib.bt_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         lib.bt_estimate_bytes.argtypes = [P, U64, U32, U32, U32, ctypes.POINTER(U64),
@@ -288,6 +315,64 @@ def bt_decompose_batch(h: Handle, graphs, flags: int = 0, max_edges_per_launch: 
     _check(h, load().bt_decompose_batch(h.ptr, arr, n, ctypes.byref(tune), ctypes.byref(st),
                                         flags | dev_flag))
     return outs, _as_dict(st)
+
+
+class Server:
+    """Continuous-batching request loop (bt_server_*).  Host buffers only; the
+    request keeps its edge array and outputs alive until it completes."""
+
+    def __init__(self, device: int = 0, memory_budget_bytes: int = 0, workers: int = 0,
+                 max_batch_graphs: int = 0, flags: int = 0):
+        lib = load()
+        cfg = ServerConfig(memory_budget_bytes, workers, max_batch_graphs, flags, 0)
+        p = ctypes.c_void_p()
+        rc = lib.bt_server_create(ctypes.byref(p), device, ctypes.byref(cfg))
+        if rc != BT_OK:
+            raise BitrussError(rc, "bt_server_create failed")
+        self.ptr = p.value
+        self._live = {}
+
+    def submit(self, edges, nU: int, nL: int, want_support: bool = False) -> int:
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        m = e.shape[0]
+        sup = np.empty(m, dtype=np.uint64) if want_support else None
+        phi = np.empty(m, dtype=np.uint32)
+        g = Graph(e.ctypes.data, m, nU, nL, sup.ctypes.data if sup is not None else None,
+                  phi.ctypes.data)
+        rid = ctypes.c_uint64()
+        rc = load().bt_server_submit(self.ptr, ctypes.byref(g), ctypes.byref(rid))
+        if rc != BT_OK:
+            raise BitrussError(rc, "bt_server_submit failed")
+        self._live[rid.value] = (e, sup, phi)
+        return rid.value
+
+    def poll(self, rid: int, wait: bool = False):
+        """Return (info dict, (support, phi) or None while pending)."""
+        info = RequestInfo()
+        rc = load().bt_server_poll(self.ptr, rid, 1 if wait else 0, ctypes.byref(info))
+        if rc != BT_OK:
+            raise BitrussError(rc, "bt_server_poll failed")
+        d = _as_dict(info)
+        if d["done"]:
+            _, sup, phi = self._live.pop(rid)
+            return d, (sup, phi)
+        return d, None
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        load().bt_server_stats_read(self.ptr, ctypes.byref(st))
+        return _as_dict(st)
+
+    def close(self):
+        if self.ptr:
+            load().bt_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def bt_profile_enable(h: Handle, on: bool = True):

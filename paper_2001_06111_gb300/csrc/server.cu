@@ -1,0 +1,251 @@
+// Request-serving loop with continuous batching (bt_server_*).
+//
+// Requests (one graph each) are queued by bt_server_submit.  Worker threads,
+// each with its own handle (stream, memory pool, device-resident index), take
+// every admissible waiting request when they become free, decompose them as
+// one batch (bt_decompose_batch: one disjoint-union pipeline), and complete
+// them.  Requests that arrive while a batch is on the GPU wait for the next
+// free worker; with two or more workers the batches overlap on the device.
+// Admission: a request's device footprint is bounded from its degrees in O(m)
+// (priority-obeyed wedges W <= sum over edges of min(d(u), d(v)), Lemma 6;
+// BE-Index bytes grow with W) and the sum over in-flight requests must stay
+// under the configured budget.  A request whose bound alone exceeds the
+// budget is rejected with BT_ERR_NOMEM.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bt_internal.cuh"
+
+namespace {
+
+struct Request {
+    uint64_t id;
+    bt_graph g;
+    uint64_t bytes;  // admission bound
+    int status = -1; // -1 pending
+    double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Upper bound on the device bytes a decomposition of g needs (host, O(m)).
+uint64_t footprint_bound(const bt_graph &g, uint32_t flags, bool device_ptrs) {
+    const uint64_t m = g.m;
+    const uint64_t n = (uint64_t)g.nU + g.nL;
+    uint64_t W = 0;
+    if (!device_ptrs && m) {
+        std::vector<uint32_t> du(g.nU, 0), dl(g.nL, 0);
+        for (uint64_t i = 0; i < m; ++i) {
+            int32_t u = g.edges[2 * i], v = g.edges[2 * i + 1];
+            if (u >= 0 && v >= 0 && (uint32_t)u < g.nU && (uint32_t)v < g.nL) {
+                du[u]++;
+                dl[v]++;
+            }
+        }
+        for (uint64_t i = 0; i < m; ++i) {
+            int32_t u = g.edges[2 * i], v = g.edges[2 * i + 1];
+            if (u >= 0 && v >= 0 && (uint32_t)u < g.nU && (uint32_t)v < g.nL)
+                W += std::min(du[u], dl[v]);
+        }
+    } else {
+        W = m * m;  // no host view of the edges: the trivial bound
+    }
+    (void)flags;
+    // CSR and sort scratch, per-edge peel state, index (pairs, bloom ids,
+    // links, death stamps, blooms) and per-SM counters
+    return (n + 1) * 32 + m * 160 + W * 32 + (64ull << 20);
+}
+
+}  // namespace
+
+struct bt_server {
+    int device = 0;
+    bt_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request *> queue;
+    std::unordered_map<uint64_t, Request *> reqs;
+    std::vector<std::thread> workers;
+    bool stop = false;
+    uint64_t next_id = 1;
+    uint64_t in_flight_bytes = 0;
+    bt_server_stats stats{};
+    std::vector<bt_handle *> handles;
+
+    void worker_main(int wi) {
+        bt_handle *h = handles[wi];
+        int rc = BT_OK;
+        std::vector<Request *> batch;
+        std::vector<bt_graph> graphs;
+        for (;;) {
+            batch.clear();
+            uint64_t bytes = 0;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+                if (queue.empty() && stop) break;
+                // admit from the head, FIFO, while the budget allows
+                while (!queue.empty()) {
+                    Request *r = queue.front();
+                    if (r->bytes > cfg.memory_budget_bytes) {  // can never fit
+                        queue.pop_front();
+                        r->status = BT_ERR_NOMEM;
+                        r->t_done = now_s();
+                        stats.rejected++;
+                        stats.completed++;
+                        cv_done.notify_all();
+                        continue;
+                    }
+                    if (in_flight_bytes + bytes + r->bytes > cfg.memory_budget_bytes) break;
+                    if (cfg.max_batch_graphs && batch.size() >= cfg.max_batch_graphs) break;
+                    queue.pop_front();
+                    bytes += r->bytes;
+                    batch.push_back(r);
+                }
+                if (batch.empty()) {
+                    // the head waits for memory held by other workers
+                    cv_work.wait_for(lk, std::chrono::milliseconds(1));
+                    continue;
+                }
+                in_flight_bytes += bytes;
+                stats.peak_in_flight_bytes = std::max(stats.peak_in_flight_bytes, in_flight_bytes);
+                stats.batches++;
+                const double t0 = now_s();
+                for (Request *r : batch) r->t_start = t0;
+            }
+            graphs.clear();
+            const double t0 = now_s();
+            for (Request *r : batch) graphs.push_back(r->g);
+            bt_batch_stats bs{};
+            rc = bt_decompose_batch(h, graphs.data(), (uint32_t)graphs.size(), nullptr, &bs,
+                                    cfg.flags & BT_TIE_LOWER_FIRST);
+            if (rc != BT_OK && graphs.size() > 1) {
+                // isolate the failing request(s): retry one by one
+                for (size_t i = 0; i < batch.size(); ++i)
+                    batch[i]->status = bt_decompose_batch(h, &graphs[i], 1, nullptr, nullptr,
+                                                          cfg.flags & BT_TIE_LOWER_FIRST);
+            } else {
+                for (Request *r : batch) r->status = rc;
+            }
+            const double t1 = now_s();
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                stats.max_batch_graphs = std::max<uint64_t>(stats.max_batch_graphs, batch.size());
+                in_flight_bytes -= bytes;
+                stats.busy_seconds += t1 - t0;
+                stats.edges += bs.edges;
+                for (Request *r : batch) {
+                    r->t_done = t1;
+                    stats.completed++;
+                }
+            }
+            cv_done.notify_all();
+            cv_work.notify_all();
+        }
+    }
+};
+
+extern "C" {
+
+int bt_server_create(bt_server **out, int device, const bt_server_config *cfg) {
+    if (!out) return BT_ERR_ARG;
+    *out = nullptr;
+    bt_server *s = new (std::nothrow) bt_server();
+    if (!s) return BT_ERR_NOMEM;
+    s->device = device;
+    if (cfg) s->cfg = *cfg;
+    if (!s->cfg.memory_budget_bytes) s->cfg.memory_budget_bytes = 120ull << 30;
+    if (!s->cfg.workers) s->cfg.workers = 2;
+    if (s->cfg.flags & ~(uint32_t)BT_TIE_LOWER_FIRST) {
+        delete s;
+        return BT_ERR_ARG;
+    }
+    for (uint32_t i = 0; i < s->cfg.workers; ++i) {
+        bt_handle *h = nullptr;
+        int rc = bt_create(&h, device, nullptr);
+        if (rc != BT_OK) {
+            for (bt_handle *x : s->handles) bt_destroy(x);
+            delete s;
+            return rc;
+        }
+        s->handles.push_back(h);
+    }
+    for (uint32_t i = 0; i < s->cfg.workers; ++i)
+        s->workers.emplace_back(&bt_server::worker_main, s, (int)i);
+    *out = s;
+    return BT_OK;
+}
+
+int bt_server_destroy(bt_server *s) {
+    if (!s) return BT_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    for (auto &t : s->workers) t.join();
+    for (bt_handle *h : s->handles) bt_destroy(h);
+    for (auto &kv : s->reqs) delete kv.second;
+    delete s;
+    return BT_OK;
+}
+
+int bt_server_submit(bt_server *s, const bt_graph *g, uint64_t *request_id) {
+    if (!s || !g || !request_id) return BT_ERR_ARG;
+    if (g->m && (!g->edges || !g->phi_out)) return BT_ERR_ARG;
+    Request *r = new (std::nothrow) Request();
+    if (!r) return BT_ERR_NOMEM;
+    r->g = *g;
+    r->bytes = footprint_bound(*g, s->cfg.flags, false);
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r->id = s->next_id++;
+        s->reqs[r->id] = r;
+        s->queue.push_back(r);
+        s->stats.submitted++;
+    }
+    s->cv_work.notify_one();
+    *request_id = r->id;
+    return BT_OK;
+}
+
+int bt_server_poll(bt_server *s, uint64_t request_id, int wait, bt_request_info *info) {
+    if (!s || !info) return BT_ERR_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) return BT_ERR_STATE;
+    Request *r = it->second;
+    if (wait) s->cv_done.wait(lk, [&] { return r->status != -1; });
+    info->done = r->status != -1;
+    info->status = r->status == -1 ? BT_OK : r->status;
+    info->queue_seconds = (r->t_start > 0 ? r->t_start : now_s()) - r->t_submit;
+    info->latency_seconds = (info->done ? r->t_done : now_s()) - r->t_submit;
+    info->admitted_bytes = r->bytes;
+    if (info->done) {  // results delivered: forget the request
+        s->reqs.erase(it);
+        delete r;
+    }
+    return BT_OK;
+}
+
+int bt_server_stats_read(bt_server *s, bt_server_stats *out) {
+    if (!s || !out) return BT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    out->queued = s->queue.size();
+    out->in_flight_bytes = s->in_flight_bytes;
+    return BT_OK;
+}
+
+}  // extern "C"

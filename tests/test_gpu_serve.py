@@ -1,0 +1,55 @@
+"""Serving with continuous batching (bt_server_*): requests that arrive while
+the GPU is busy are batched together, and every result equals the graph's
+decomposition alone."""
+import numpy as np
+import pytest
+
+from paper_2001_06111_gb300 import bitruss as bt
+from paper_2001_06111_gb300 import build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def alone():
+    build.build()
+    h = bt.bt_create(0)
+    yield lambda e, nU, nL: bt.bt_decompose(h, e, nU, nL)[:2]
+    h.close()
+
+
+def test_requests_batched_while_busy_and_exact(alone):
+    big = synth.vertex_sample(synth.medium(), 0.5, 3)  # keeps the worker busy
+    small = [synth.batch_graph(i, hi=20000) for i in range(30)]
+    with bt.Server(0, workers=1) as srv:
+        ids = [srv.submit(big.edges, big.nU, big.nL, want_support=True)]
+        ids += [srv.submit(g.edges, g.nU, g.nL, want_support=True) for g in small]
+        results = [srv.poll(i, wait=True) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == 31 and st["rejected"] == 0
+    assert st["max_batch_graphs"] >= 2 and st["batches"] < 31
+    for (info, (sup, phi)), g in zip(results, [big] + small):
+        assert info["status"] == bt.BT_OK
+        s1, p1 = alone(g.edges, g.nU, g.nL)
+        np.testing.assert_array_equal(sup, s1)
+        np.testing.assert_array_equal(phi, p1)
+
+
+def test_concurrent_workers_exact(alone):
+    gs = [synth.batch_graph(100 + i, hi=50000) for i in range(24)]
+    with bt.Server(0, workers=2) as srv:
+        ids = [srv.submit(g.edges, g.nU, g.nL) for g in gs]
+        res = [srv.poll(i, wait=True) for i in ids]
+    for (info, (_, phi)), g in zip(res, gs):
+        assert info["status"] == bt.BT_OK and info["latency_seconds"] >= info["queue_seconds"] >= 0
+        np.testing.assert_array_equal(phi, alone(g.edges, g.nU, g.nL)[1])
+
+
+def test_admission_rejects_oversized_request():
+    build.build()
+    g = synth.small()
+    with bt.Server(0, memory_budget_bytes=1 << 20, workers=1) as srv:
+        rid = srv.submit(g.edges, g.nU, g.nL)
+        info, _ = srv.poll(rid, wait=True)
+        assert info["status"] == bt.BT_ERR_NOMEM
+        assert srv.stats()["rejected"] == 1
