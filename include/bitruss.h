@@ -215,10 +215,15 @@ typedef struct {
     uint32_t *phi_out;      /* uint32[m] */
 } bt_graph;
 
-/* Batch schedule.  Zero fields are chosen by the library. */
+/* Batch schedule.  Zero fields are chosen by the library: the autotuner
+ * times candidate schedules on a sample of the batch (about 8M edges of its
+ * graphs) and caches the winner in the handle per batch signature (log4 of
+ * the total edges and of the largest graph). */
 typedef struct {
     uint64_t max_edges_per_launch;  /* graphs are packed into unions of at most this many edges */
-    uint32_t reserved[4];
+    uint32_t count_threads;         /* wedge-count / index block size: 256, 512 or 1024 */
+    uint32_t peel_item;             /* peel work item: 32 or 64 links / pair slots per warp */
+    uint32_t reserved[2];
 } bt_tune;
 
 typedef struct {
@@ -228,6 +233,10 @@ typedef struct {
     uint64_t wedges;           /* total priority-obeyed wedges */
     uint64_t rounds, levels;   /* peeling rounds and levels, summed over unions */
     uint64_t support_updates;
+    uint32_t count_threads;    /* schedule used */
+    uint32_t peel_item;
+    uint32_t tuned;            /* 1 if this call ran the autotuner, 2 if it used a cached choice */
+    uint32_t reserved;
 } bt_batch_stats;
 
 /*

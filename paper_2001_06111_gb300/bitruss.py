@@ -78,14 +78,17 @@ class Graph(ctypes.Structure):
 
 
 class Tune(ctypes.Structure):
-    _fields_ = [("max_edges_per_launch", ctypes.c_uint64), ("reserved", ctypes.c_uint32 * 4)]
+    _fields_ = [("max_edges_per_launch", ctypes.c_uint64), ("count_threads", ctypes.c_uint32),
+                ("peel_item", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class BatchStats(ctypes.Structure):
     _fields_ = [("graphs", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("edges", ctypes.c_uint64), ("wedges", ctypes.c_uint64),
                 ("rounds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
-                ("support_updates", ctypes.c_uint64)]
+                ("support_updates", ctypes.c_uint64), ("count_threads", ctypes.c_uint32),
+                ("peel_item", ctypes.c_uint32), ("tuned", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -292,7 +295,7 @@ def bt_count_support_static(d_edges, nU: int, nL: int, d_support_out, flags: int
 
 
 def bt_decompose_batch(h: Handle, graphs, flags: int = 0, max_edges_per_launch: int = 0,
-                       want_support: bool = True):
+                       want_support: bool = True, count_threads: int = 0, peel_item: int = 0):
     """Decompose a list of graphs, each given as (edges, nU, nL) with numpy
     (host) or CUDA torch (device) edge lists; returns ([(support, phi)], stats)."""
     n = len(graphs)
@@ -310,7 +313,7 @@ def bt_decompose_batch(h: Handle, graphs, flags: int = 0, max_edges_per_launch: 
         phi, pptr = _out(dev, m, np.uint32, _torch_dtype("uint32"), None)
         arr[i] = Graph(ptr, m, nU, nL, sptr, pptr)
         outs.append((sup, phi))
-    tune = Tune(max_edges_per_launch)
+    tune = Tune(max_edges_per_launch, count_threads, peel_item)
     st = BatchStats()
     _check(h, load().bt_decompose_batch(h.ptr, arr, n, ctypes.byref(tune), ctypes.byref(st),
                                         flags | dev_flag))

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -23,6 +24,9 @@ struct bt_handle {
     std::string err;
     bt::Prof prof;
     bt_profile last{};
+    int count_nt = 512;   // schedule used by the next pipeline run
+    int peel_seg = 32;
+    std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (count_nt, peel_seg)
 };
 
 namespace {
@@ -162,7 +166,7 @@ int count_and_index(bt_handle *h, Prepared &P, uint64_t *d_support, bool want_in
         co.nbv = al.get<uint64_t>(P.g.n);
         if (al.err != cudaSuccess) return cuda_fail(h, al.err, "allocating count buffers");
     }
-    cudaError_t e = bt::count_wedges(P.g, co, h->num_sms, al);
+    cudaError_t e = bt::count_wedges(P.g, co, h->num_sms, al, h->count_nt);
     if (e != cudaSuccess) return cuda_fail(h, e, "counting wedges");
     unsigned long long bf = 0;
     e = cudaMemcpyAsync(&bf, co.butterflies_dev, sizeof(bf), cudaMemcpyDeviceToHost, h->stream);
@@ -182,7 +186,7 @@ int count_and_index(bt_handle *h, Prepared &P, uint64_t *d_support, bool want_in
         al.put(tot);
         al.put(scratch);
         if (e != cudaSuccess) return cuda_fail(h, e, "summing wedges");
-        e = bt::emit_index(P.g, co, ix, h->num_sms, al, h->stream);
+        e = bt::emit_index(P.g, co, ix, h->num_sms, al, h->stream, h->count_nt);
         al.put(co.inc_cnt);
         al.put(co.w2v);
         al.put(co.nbv);
@@ -394,7 +398,7 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
     rc = build_index_impl(h, edges, m, nU, nL, flags, d_sup, al);
     bt::PeelResult pr;
     if (rc == BT_OK) {
-        cudaError_t e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al);
+        cudaError_t e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al, h->peel_seg);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
         else if (pr.status == BT_ERR_OVERFLOW)
             rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
@@ -511,7 +515,7 @@ static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uin
                               (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, d_sup, al);
     bt::PeelResult pr;
     if (rc == BT_OK && M > 0) {
-        e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al);
+        e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al, h->peel_seg);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
         else if (pr.status == BT_ERR_OVERFLOW)
             rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
@@ -574,6 +578,71 @@ static int decompose_packed(bt_handle *h, const bt_graph *graphs, uint32_t n, ui
     return BT_OK;
 }
 
+// Elapsed ms between the profiler events of a phase (0 if not recorded).
+static float phase_ms(bt_handle *h, int phase) {
+    float ms = 0.f;
+    if (!h->prof.used[phase] ||
+        cudaEventElapsedTime(&ms, h->prof.ev[2 * phase], h->prof.ev[2 * phase + 1]) != cudaSuccess)
+        return 0.f;
+    return ms;
+}
+
+// Picks the count block size and the peel item size for this batch: looks up
+// the handle's cache by signature, else times three candidate schedules on a
+// sample of the graphs (writing the sample graphs' outputs, which the real
+// run overwrites with the same values) and caches the fastest parts.
+static int autotune(bt_handle *h, const bt_graph *graphs, uint32_t n, uint32_t flags, bt::Alloc &al,
+                    uint32_t *tuned) {
+    uint64_t total = 0, mx = 0;
+    for (uint32_t g = 0; g < n; ++g) {
+        total += graphs[g].m;
+        mx = std::max<uint64_t>(mx, graphs[g].m);
+    }
+    // coarse buckets (powers of 4) so that similar batches share a choice
+    const uint64_t sig = ((uint64_t)(bt::bits_for(total) / 2) << 8) | (uint64_t)(bt::bits_for(mx) / 2);
+    auto it = h->tuned.find(sig);
+    if (it != h->tuned.end()) {
+        h->count_nt = it->second.first;
+        h->peel_seg = it->second.second;
+        *tuned = 2;
+        return BT_OK;
+    }
+    if (total == 0) return BT_OK;
+    // sample: every stride-th graph, about 8M edges
+    const uint64_t target = 8ull << 20;
+    const uint32_t stride = (uint32_t)std::max<uint64_t>(1, (total + target - 1) / target);
+    std::vector<bt_graph> sample;
+    for (uint32_t g = 0; g < n; g += stride) sample.push_back(graphs[g]);
+    const bool prof_was_on = h->prof.on;
+    if (!h->prof.ev[0]) {
+        for (auto &ev : h->prof.ev)
+            if (cudaEventCreate(&ev) != cudaSuccess) return cuda_fail(h, cudaErrorUnknown, "creating events");
+    }
+    h->prof.on = true;
+    const int cand[3][2] = {{512, 32}, {256, 64}, {1024, 32}};
+    float t_build[3] = {0, 0, 0}, t_peel[3] = {0, 0, 0};
+    int rc = BT_OK;
+    for (int c = 0; c < 3 && rc == BT_OK; ++c) {
+        h->count_nt = cand[c][0];
+        h->peel_seg = cand[c][1];
+        for (bool &u : h->prof.used) u = false;
+        rc = decompose_union(h, sample.data(), (uint32_t)sample.size(), flags, nullptr, al);
+        t_build[c] = phase_ms(h, bt::kPhCount) + phase_ms(h, bt::kPhEmit);
+        t_peel[c] = phase_ms(h, bt::kPhPeel);
+    }
+    h->prof.on = prof_was_on;
+    if (rc != BT_OK) return rc;
+    int best = 0;
+    for (int c = 1; c < 3; ++c)
+        if (t_build[c] < t_build[best]) best = c;
+    const float peel32 = 0.5f * (t_peel[0] + t_peel[2]);
+    h->count_nt = cand[best][0];
+    h->peel_seg = t_peel[1] < peel32 ? 64 : 32;
+    h->tuned[sig] = {h->count_nt, h->peel_seg};
+    *tuned = 1;
+    return BT_OK;
+}
+
 int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const bt_tune *tune,
                        bt_batch_stats *stats, uint32_t flags) {
     if (!h) return BT_ERR_ARG;
@@ -594,7 +663,23 @@ int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const b
     bt::Alloc al = make_alloc(h);
     call_begin(h, al, 0, 0);
     bt_batch_stats acc{};
-    int rc = decompose_packed(h, graphs, n, cap, flags, &acc, al);
+    const int saved_nt = h->count_nt, saved_seg = h->peel_seg;
+    uint32_t tuned = 0;
+    int rc = BT_OK;
+    if (tune && tune->count_threads && tune->peel_item) {
+        h->count_nt = tune->count_threads;
+        h->peel_seg = tune->peel_item;
+    } else {
+        rc = autotune(h, graphs, n, flags, al, &tuned);
+        if (tune && tune->count_threads) h->count_nt = tune->count_threads;
+        if (tune && tune->peel_item) h->peel_seg = tune->peel_item;
+    }
+    if (rc == BT_OK) rc = decompose_packed(h, graphs, n, cap, flags, &acc, al);
+    acc.count_threads = (uint32_t)h->count_nt;
+    acc.peel_item = (uint32_t)h->peel_seg;
+    acc.tuned = tuned;
+    h->count_nt = saved_nt;
+    h->peel_seg = saved_seg;
     call_end(h, al);
     if (rc == BT_OK) {
         h->last.n_edges = acc.edges;

@@ -118,7 +118,8 @@ struct CountOut {
     uint64_t *nbv = nullptr;      // [n] blooms per start vertex (index mode)
     unsigned long long *butterflies_dev = nullptr;  // [1] set by count_wedges; caller frees
 };
-cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al);
+// nt: count block size (256, 512 or 1024; anything else means 512)
+cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt = 512);
 
 // Device-resident BE-Index (Section IV-A).
 struct Index {
@@ -138,7 +139,7 @@ struct Index {
     }
 };
 cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, Alloc &al,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int nt = 512);
 void free_index(Index &ix, Alloc &al);
 
 // ---------------------------------------------------------------- peeling
@@ -147,8 +148,9 @@ struct PeelResult {
     int status = BT_OK;
 };
 // support: [m] initial supports (device, preserved); phi_out: [m] device.
+// seg: peel work-item size (32 or 64 entries; anything else means 32)
 cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
-                 int num_sms, Alloc &al);
+                 int num_sms, Alloc &al, int seg = 32);
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int bits_for(uint64_t maxval) {

@@ -14,7 +14,8 @@
 //
 // Work layout: persistent blocks pull start vertices from a global queue in
 // decreasing rank (heaviest first).  A block enumerates the wedges of its
-// vertex in chunks of kThreads middle vertices: a block scan of the per-arc
+// vertex in chunks of NT middle vertices (NT = block size, picked by the
+// batch autotuner from 256, 512, 1024): a block scan of the per-arc
 // prefix lengths flattens the chunk's wedges, so every thread handles whole
 // wedges regardless of the degree skew.  Counters are a dense per-block
 // array indexed by rank, kept at zero between vertices (it is reset by the
@@ -25,17 +26,17 @@
 namespace bt {
 namespace {
 
-constexpr int kThreads = 512;
-
+template <int NT>
 struct Chunk {
-    uint32_t off[kThreads + 1];  // exclusive prefix of wedge counts; off[kThreads] = total
-    uint32_t v[kThreads];        // middle vertex (rank)
-    uint32_t e[kThreads];        // edge id of (u, v)
+    uint32_t off[NT + 1];  // exclusive prefix of wedge counts; off[NT] = total
+    uint32_t v[NT];        // middle vertex (rank)
+    uint32_t e[NT];        // edge id of (u, v)
 };
 
-// Loads middle vertices [c0, c0 + kThreads) of start vertex u.  Returns the
+// Loads middle vertices [c0, c0 + NT) of start vertex u.  Returns the
 // number of wedges in the chunk.  Contains __syncthreads().
-__device__ __forceinline__ uint32_t load_chunk(Chunk &ch, const uint32_t *adj, const uint32_t *eid,
+template <int NT>
+__device__ __forceinline__ uint32_t load_chunk(Chunk<NT> &ch, const uint32_t *adj, const uint32_t *eid,
                                                const uint32_t *pl, uint64_t a, uint32_t h,
                                                uint32_t c0) {
     uint32_t i = c0 + threadIdx.x;
@@ -50,15 +51,16 @@ __device__ __forceinline__ uint32_t load_chunk(Chunk &ch, const uint32_t *adj, c
     ch.off[threadIdx.x] = ex;
     ch.v[threadIdx.x] = v;
     ch.e[threadIdx.x] = e;
-    if (threadIdx.x == 0) ch.off[kThreads] = tot;
+    if (threadIdx.x == 0) ch.off[NT] = tot;
     __syncthreads();
     return tot;
 }
 
 // Wedge t of the chunk -> (chunk slot vi, arc index of (v, w) in the CSR).
-__device__ __forceinline__ uint64_t wedge_arc(const Chunk &ch, const uint64_t *off, uint32_t t,
+template <int NT>
+__device__ __forceinline__ uint64_t wedge_arc(const Chunk<NT> &ch, const uint64_t *off, uint32_t t,
                                               uint32_t &vi) {
-    vi = dev::last_le_u32(ch.off, kThreads, t);
+    vi = dev::last_le_u32(ch.off, NT, t);
     return off[ch.v[vi]] + (t - ch.off[vi]);
 }
 
@@ -73,12 +75,13 @@ __device__ __forceinline__ uint32_t next_vertex(uint32_t *queue, uint32_t n, uin
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
 
 // Pass A over all chunks of u.
-__device__ void pass_count(Chunk &ch, const uint64_t *off, const uint32_t *adj,
+template <int NT>
+__device__ void pass_count(Chunk<NT> &ch, const uint64_t *off, const uint32_t *adj,
                            const uint32_t *eid, const uint32_t *pl, uint64_t a, uint32_t h,
                            uint32_t *cnt) {
-    for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+    for (uint32_t c0 = 0; c0 < h; c0 += NT) {
         uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
-        for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+        for (uint32_t t = threadIdx.x; t < T; t += NT) {
             uint32_t vi;
             uint64_t arc = wedge_arc(ch, off, t, vi);
             atomicAdd(&cnt[adj[arc]], 1u);
@@ -87,16 +90,16 @@ __device__ void pass_count(Chunk &ch, const uint64_t *off, const uint32_t *adj,
     }
 }
 
-template <bool kIndex>
-__global__ void __launch_bounds__(kThreads) k_count(
+template <bool kIndex, int NT>
+__global__ void __launch_bounds__(NT) k_count(
     const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
     const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
     const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
     uint32_t *cnt_all, unsigned long long *support, uint32_t *inc_cnt, uint64_t *w2v,
     uint64_t *nbv, unsigned long long *totals, uint32_t *queue) {
-    __shared__ Chunk ch;
-    __shared__ unsigned long long s_acc[kThreads];
-    __shared__ uint32_t s_inc[kThreads];
+    __shared__ Chunk<NT> ch;
+    __shared__ unsigned long long s_acc[NT];
+    __shared__ uint32_t s_inc[NT];
     __shared__ uint32_t s_q;
     uint32_t *cnt = cnt_all + (size_t)blockIdx.x * n;
     s_acc[threadIdx.x] = 0;
@@ -117,9 +120,9 @@ __global__ void __launch_bounds__(kThreads) k_count(
         pass_count(ch, off, adj, eid, pl, a, h, cnt);
         // pass B: attribute c-1 to both edges of every wedge in a bloom
         unsigned long long w2_local = 0;
-        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+        for (uint32_t c0 = 0; c0 < h; c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
-            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+            for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 uint32_t c = ld_cg(&cnt[adj[arc]]);
@@ -147,9 +150,9 @@ __global__ void __launch_bounds__(kThreads) k_count(
         }
         // pass C: reset counters; the first thread to clear a bloom counts it
         unsigned long long nb_local = 0;
-        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+        for (uint32_t c0 = 0; c0 < h; c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
-            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+            for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 uint32_t old = atomicExch(&cnt[adj[arc]], 0u);
@@ -175,7 +178,8 @@ __global__ void __launch_bounds__(kThreads) k_count(
 
 // Emit the index: blooms (bloom number, first pair), twin pairs and the
 // per-edge link lists.  aux_all is a second dense per-block array.
-__global__ void __launch_bounds__(kThreads) k_emit(
+template <int NT>
+__global__ void __launch_bounds__(NT) k_emit(
     const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
     const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
     const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     const uint64_t *__restrict__ pair_base, const uint64_t *__restrict__ inc_off,
     uint32_t *inc_fill, uint32_t *bloom_k, uint32_t *bloom_off, uint2 *pairs,
     uint32_t *pair_bloom, uint32_t *inc, uint32_t *queue) {
-    __shared__ Chunk ch;
+    __shared__ Chunk<NT> ch;
     __shared__ uint32_t s_q;
     // bloom count (high 32 bits) and pair count (low 32 bits) of the vertex,
     // advanced by one atomic so that pair ranges follow bloom ids
@@ -201,9 +205,9 @@ __global__ void __launch_bounds__(kThreads) k_emit(
         if (threadIdx.x == 0) s_alloc = 0;
         pass_count(ch, off, adj, eid, pl, a, h, cnt);
         // claim: one thread per bloom allocates its id and pair range
-        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+        for (uint32_t c0 = 0; c0 < h; c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
-            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+            for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 uint32_t w = adj[arc];
@@ -221,9 +225,9 @@ __global__ void __launch_bounds__(kThreads) k_emit(
             __syncthreads();
         }
         // place each bloom wedge as a twin pair and link both edges to it
-        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+        for (uint32_t c0 = 0; c0 < h; c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
-            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+            for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 uint32_t w = adj[arc];
@@ -244,9 +248,9 @@ __global__ void __launch_bounds__(kThreads) k_emit(
             __syncthreads();
         }
         // reset: blooms already drained cnt to zero; clear aux and single wedges
-        for (uint32_t c0 = 0; c0 < h; c0 += kThreads) {
+        for (uint32_t c0 = 0; c0 < h; c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
-            for (uint32_t t = threadIdx.x; t < T; t += kThreads) {
+            for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 uint32_t w = adj[arc];
@@ -258,18 +262,36 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     }
 }
 
+template <int NT>
 int blocks_per_sm_count() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_count<true>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_count<true, NT>, NT, 0);
     return b > 0 ? b : 1;
+}
+
+int blocks_per_sm_for(int nt) {
+    return nt == 256 ? blocks_per_sm_count<256>()
+                     : nt == 1024 ? blocks_per_sm_count<1024>() : blocks_per_sm_count<512>();
+}
+
+template <int NT>
+void launch_count(bool index, unsigned blocks, const Csr &g, uint32_t *cnt, unsigned long long *sup,
+                  CountOut &o, unsigned long long *totals, uint32_t *queue, cudaStream_t st) {
+    if (index)
+        k_count<true, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, cnt, sup,
+                                                  o.inc_cnt, o.w2v, o.nbv, totals, queue);
+    else
+        k_count<false, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, cnt, sup,
+                                                   nullptr, nullptr, nullptr, totals, queue);
 }
 
 }  // namespace
 
-cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al) {
+cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt) {
     const bool index = o.inc_cnt != nullptr;
     const uint32_t n = g.n;
-    int bps = blocks_per_sm_count();
+    if (nt != 256 && nt != 1024) nt = 512;
+    int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
     uint32_t *cnt = al.get<uint32_t>((size_t)blocks * n);
     uint32_t *queue = al.get<uint32_t>(1);
@@ -282,15 +304,9 @@ cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al) {
     if (index) BT_CUDA(cudaMemsetAsync(o.inc_cnt, 0, sizeof(uint32_t) * g.m, al.stream));
     auto *sup = reinterpret_cast<unsigned long long *>(o.support);
     al.mark(kPhCount, false);
-    if (index) {
-        k_count<true><<<blocks, kThreads, 0, al.stream>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n,
-                                                          cnt, sup, o.inc_cnt, o.w2v, o.nbv,
-                                                          totals, queue);
-    } else {
-        k_count<false><<<blocks, kThreads, 0, al.stream>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n,
-                                                           cnt, sup, nullptr, nullptr, nullptr,
-                                                           totals, queue);
-    }
+    if (nt == 256) launch_count<256>(index, blocks, g, cnt, sup, o, totals, queue, al.stream);
+    else if (nt == 1024) launch_count<1024>(index, blocks, g, cnt, sup, o, totals, queue, al.stream);
+    else launch_count<512>(index, blocks, g, cnt, sup, o, totals, queue, al.stream);
     al.launches++;
     al.mark(kPhCount, true);
     BT_CUDA(cudaGetLastError());
@@ -301,7 +317,8 @@ cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al) {
 }
 
 cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, Alloc &al,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int nt) {
+    if (nt != 256 && nt != 1024) nt = 512;
     const uint32_t n = g.n;
     const uint64_t m = g.m;
     ix.m = m;
@@ -335,7 +352,7 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     ix.pair_bloom = al.get<uint32_t>(ix.w2);
     ix.inc = al.get<uint32_t>(2 * ix.w2);
     uint32_t *inc_fill = al.get<uint32_t>(m);
-    int bps = blocks_per_sm_count();
+    int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
     uint32_t *cnt = al.get<uint32_t>((size_t)blocks * n);
     uint32_t *aux = al.get<uint32_t>((size_t)blocks * n);
@@ -349,10 +366,13 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     BT_CUDA(cudaMemsetAsync(aux, 0, sizeof(uint32_t) * (size_t)blocks * n, al.stream));
     BT_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), al.stream));
     al.mark(kPhEmit, false);
-    k_emit<<<blocks, kThreads, 0, al.stream>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, cnt, aux,
-                                               bloom_base, pair_base, ix.inc_off, inc_fill,
-                                               ix.bloom_k, ix.bloom_off, ix.pairs, ix.pair_bloom,
-                                               ix.inc, queue);
+#define BT_EMIT_ARGS                                                                         \
+    g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, cnt, aux, bloom_base, pair_base, ix.inc_off,  \
+        inc_fill, ix.bloom_k, ix.bloom_off, ix.pairs, ix.pair_bloom, ix.inc, queue
+    if (nt == 256) k_emit<256><<<blocks, 256, 0, al.stream>>>(BT_EMIT_ARGS);
+    else if (nt == 1024) k_emit<1024><<<blocks, 1024, 0, al.stream>>>(BT_EMIT_ARGS);
+    else k_emit<512><<<blocks, 512, 0, al.stream>>>(BT_EMIT_ARGS);
+#undef BT_EMIT_ARGS
     al.launches++;
     al.mark(kPhEmit, true);
     BT_CUDA(cudaGetLastError());

@@ -40,7 +40,10 @@ namespace bt {
 namespace {
 
 constexpr int kPeelThreads = 1024;
-constexpr uint32_t kSeg = 32;                     // entries per work item (one per lane)
+// entries per work item: SEG = 32 or 64 (template parameter picked by the
+// batch autotuner); each lane handles SEG / 32 entries with their loads and
+// atomics issued together.
+constexpr uint32_t kMaxSeg = 64;
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
 constexpr uint32_t kErrBarrier = 1u;
 constexpr uint32_t kErrRounds = 2u;
@@ -152,6 +155,7 @@ __device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no) {
 
 // Queue edge e (links [ib, ie)) for the round `next_round`: one incidence
 // item per kSeg links, each carrying its link range.
+template <uint32_t kSeg>
 __device__ __forceinline__ void push_edge(const PeelArgs &a, uint32_t e, uint32_t dst,
                                           uint32_t next_round, uint64_t ib, uint64_t ie, long long k) {
     a.state[e] = next_round;
@@ -175,6 +179,7 @@ __device__ __forceinline__ void push_near(const PeelArgs &a, uint32_t e, uint32_
 
 // Subtract dec from support(e).  Queue e for the next round when this takes
 // it from > k to <= k, and list it in the near window when it falls below khi.
+template <uint32_t kSeg>
 __device__ __forceinline__ void decrement(const PeelArgs &a, uint32_t e, long long dec, const Lvl &L,
                                           uint32_t dst, uint32_t next_round, bool have_range,
                                           uint64_t ib, uint64_t ie) {
@@ -186,7 +191,7 @@ __device__ __forceinline__ void decrement(const PeelArgs &a, uint32_t e, long lo
             ib = a.inc_off[e];
             ie = a.inc_off[e + 1];
         }
-        push_edge(a, e, dst, next_round, ib, ie, L.k);
+        push_edge<kSeg>(a, e, dst, next_round, ib, ie, L.k);
     }
     if (old >= L.khi && now < L.khi) push_near(a, e, L.nq);
 }
@@ -196,7 +201,9 @@ __device__ __forceinline__ long long window_top(long long kmin) {
     return kmin + (w < 16 ? 16 : w);
 }
 
+template <uint32_t kSeg>
 __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
+    constexpr uint32_t R = kSeg / 32;  // entries per lane
     const int lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             for (uint32_t i = gtid; i < nn2; i += nthreads) {
                 const uint32_t e = ldcg_u32(&a.near[L.nq][i]);
                 if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k)
-                    push_edge(a, e, par, round, a.inc_off[e], a.inc_off[e + 1], L.k);
+                    push_edge<kSeg>(a, e, par, round, a.inc_off[e], a.inc_off[e + 1], L.k);
             }
             if (gtid == 0) atomicAdd(&ctl->levels, 1ull);
             if (!grid_barrier(ctl, bar_no)) break;
@@ -330,23 +337,37 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             for (uint32_t i = gwarp; i < n_items; i += nwarps) {
                 const uint4 it = i == gwarp ? it0 : __ldcg(&a.items[par][i]);
                 const uint32_t cnt = it.w & 0x7FFFFFFFu;
-                if ((uint32_t)lane >= cnt) continue;
-                const uint64_t j = ((uint64_t)it.z << 32 | it.y) + lane;
-                const uint32_t p = a.inc[j];
-                const uint32_t B = a.pair_bloom[p];
-                // the first edge of S to stamp the pair kills it (once)
-                if (atomicCAS(&a.died[p], kAlive, round) != kAlive) continue;
-                const uint32_t bkB = ldcg_u32(&a.bk[B]);
-                const uint32_t bo0 = a.bloom_off[B], bo1 = a.bloom_off[B + 1];
-                if (atomicAdd(&C[B], 1u) == 0u) {
-                    const uint32_t span = bo1 - bo0;
-                    const uint32_t nseg = (span + kSeg - 1) / kSeg;
-                    const uint32_t base = atomicAdd(&ctl->n_bseg[c3], nseg);
-                    for (uint32_t s = 0; s < nseg; ++s) {
-                        const uint32_t left = span - s * kSeg;
-                        a.bseg[c3][base + s] = make_uint4(
-                            B, bo0 + s * kSeg, (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u),
-                            bkB);
+                const uint64_t j0 = ((uint64_t)it.z << 32 | it.y) + lane;
+                uint32_t p[R], B[R];
+                bool won[R];
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r) {
+                    const bool act = lane + 32u * r < cnt;
+                    p[r] = act ? a.inc[j0 + 32u * r] : 0u;
+                    won[r] = act;
+                }
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r)
+                    if (won[r]) B[r] = a.pair_bloom[p[r]];
+                // the first edge of S to stamp a pair kills it (once)
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r)
+                    if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r) {
+                    if (!won[r]) continue;
+                    const uint32_t bkB = ldcg_u32(&a.bk[B[r]]);
+                    const uint32_t bo0 = a.bloom_off[B[r]], bo1 = a.bloom_off[B[r] + 1];
+                    if (atomicAdd(&C[B[r]], 1u) == 0u) {
+                        const uint32_t span = bo1 - bo0;
+                        const uint32_t nseg = (span + kSeg - 1) / kSeg;
+                        const uint32_t base = atomicAdd(&ctl->n_bseg[c3], nseg);
+                        for (uint32_t s = 0; s < nseg; ++s) {
+                            const uint32_t left = span - s * kSeg;
+                            a.bseg[c3][base + s] = make_uint4(
+                                B[r], bo0 + s * kSeg,
+                                (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u), bkB);
+                        }
                     }
                 }
             }
@@ -366,25 +387,34 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 const uint32_t c = ldcg_u32(&C[B]);
                 if ((it.z >> 31) && lane == 0) a.bk[B] = kB - c;
                 if (lane == 0) slots += cnt;
-                if ((uint32_t)lane >= cnt) continue;
-                const uint32_t p = it.y + lane;
-                const uint32_t d = ldcg_u32(&a.died[p]);
-                const uint2 pr = a.pairs[p];
-                if (d == kAlive) {
-                    // a surviving pair: one butterfly lost per dead pair
-                    decrement(a, pr.x, c, L, np, round + 1, false, 0, 0);
-                    decrement(a, pr.y, c, L, np, round + 1, false, 0, 0);
-                    upd += 2;
-                } else if (d == round && kB > 1u) {
-                    // died now: a member outside S loses its k_B - 1 butterflies
-                    const uint32_t sx = ldcg_u32(&a.state[pr.x]), sy = ldcg_u32(&a.state[pr.y]);
-                    if (sx != round) {
-                        decrement(a, pr.x, (long long)kB - 1, L, np, round + 1, false, 0, 0);
-                        ++upd;
-                    }
-                    if (sy != round) {
-                        decrement(a, pr.y, (long long)kB - 1, L, np, round + 1, false, 0, 0);
-                        ++upd;
+                uint32_t d[R];
+                uint2 pr[R];
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r) {
+                    const bool act = lane + 32u * r < cnt;
+                    const uint32_t pp = it.y + lane + 32u * r;
+                    d[r] = act ? ldcg_u32(&a.died[pp]) : round + 1u;  // inactive: neither case below
+                    pr[r] = act ? a.pairs[pp] : make_uint2(0, 0);
+                }
+#pragma unroll
+                for (uint32_t r = 0; r < R; ++r) {
+                    if (d[r] == kAlive) {
+                        // a surviving pair: one butterfly lost per dead pair
+                        decrement<kSeg>(a, pr[r].x, c, L, np, round + 1, false, 0, 0);
+                        decrement<kSeg>(a, pr[r].y, c, L, np, round + 1, false, 0, 0);
+                        upd += 2;
+                    } else if (d[r] == round && kB > 1u) {
+                        // died now: a member outside S loses its k_B - 1 butterflies
+                        const uint32_t sx = ldcg_u32(&a.state[pr[r].x]);
+                        const uint32_t sy = ldcg_u32(&a.state[pr[r].y]);
+                        if (sx != round) {
+                            decrement<kSeg>(a, pr[r].x, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+                            ++upd;
+                        }
+                        if (sy != round) {
+                            decrement<kSeg>(a, pr[r].y, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+                            ++upd;
+                        }
                     }
                 }
             }
@@ -430,7 +460,8 @@ inline unsigned grid_for(uint64_t items, int threads, unsigned cap) {
 }  // namespace
 
 cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
-                 int num_sms, Alloc &al) {
+                 int num_sms, Alloc &al, int seg) {
+    const uint32_t kSeg = seg == 64 ? 64u : 32u;
     const uint64_t m = ix.m;
     res = PeelResult{};
     if (m == 0) return cudaSuccess;
@@ -478,11 +509,12 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     h.minsup2 = ~0ull;
     BT_CUDA(cudaMemcpyAsync(a.ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     int bps = 0;
-    BT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_peel, kPeelThreads, 0));
+    void *kfn = kSeg == 64 ? (void *)k_peel<64> : (void *)k_peel<32>;
+    BT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, kPeelThreads, 0));
     if (bps < 1) return cudaErrorCooperativeLaunchTooLarge;
     dim3 grid((unsigned)(num_sms * bps)), block(kPeelThreads);
     void *kargs[] = {&a};
-    BT_CUDA(cudaLaunchCooperativeKernel((void *)k_peel, grid, block, kargs, 0, st));
+    BT_CUDA(cudaLaunchCooperativeKernel(kfn, grid, block, kargs, 0, st));
     al.launches++;
     BT_CUDA(cudaMemcpyAsync(&h, a.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     BT_CUDA(cudaStreamSynchronize(st));

@@ -105,3 +105,24 @@ def test_batch_reports_bad_graph(h):
     # handle still usable
     outs, _ = bt.bt_decompose_batch(h, gs[:4])
     assert len(outs) == 4
+
+
+def test_autotuner_choice_cached_and_schedules_exact(h):
+    gs = mixed_graphs()
+    h2 = bt.bt_create(0)
+    try:
+        first, st1 = bt.bt_decompose_batch(h2, gs)
+        again, st2 = bt.bt_decompose_batch(h2, gs)
+    finally:
+        h2.close()
+    assert st1["tuned"] == 1 and st2["tuned"] == 2
+    assert st1["count_threads"] in (256, 512, 1024) and st1["peel_item"] in (32, 64)
+    assert (st1["count_threads"], st1["peel_item"]) == (st2["count_threads"], st2["peel_item"])
+    for nt, seg in ((256, 64), (1024, 32), (512, 64)):
+        forced, st = bt.bt_decompose_batch(h, gs, count_threads=nt, peel_item=seg)
+        assert st["tuned"] == 0 and (st["count_threads"], st["peel_item"]) == (nt, seg)
+        for (s0, p0), (s1, p1) in zip(first, forced):
+            np.testing.assert_array_equal(s0, s1)
+            np.testing.assert_array_equal(p0, p1)
+        for (s0, p0), (s1, p1) in zip(first, again):
+            np.testing.assert_array_equal(p0, p1)
