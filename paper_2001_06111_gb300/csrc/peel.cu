@@ -43,7 +43,11 @@ constexpr int kPeelThreads = 1024;
 // entries per work item: SEG = 32 or 64 (template parameter picked by the
 // batch autotuner); each lane handles SEG / 32 entries with their loads and
 // atomics issued together.
-constexpr uint32_t kMaxSeg = 64;
+// items with at most kSmall entries are processed by one lane each, larger
+// ones by the whole warp.  Lane l of warp w takes item w + l * nwarps (plus
+// multiples of 32 * nwarps): a round with fewer items than warps still gives
+// every item its own warp, and a large round fills all lanes.
+constexpr uint32_t kSmall = 2;
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
 constexpr uint32_t kErrBarrier = 1u;
 constexpr uint32_t kErrRounds = 2u;
@@ -201,6 +205,50 @@ __device__ __forceinline__ long long window_top(long long kmin) {
     return kmin + (w < 16 ? 16 : w);
 }
 
+// Incidence phase, one killed pair of bloom B: count it in C(B) and, for the
+// first kill of B this round, queue B's pairs as bloom items (each records the
+// bloom number k_B at round start).
+template <uint32_t kSeg>
+__device__ __forceinline__ void count_kill(const PeelArgs &a, uint32_t *C, uint32_t B, uint32_t c3) {
+    const uint32_t bkB = __ldcg(&a.bk[B]);
+    const uint32_t bo0 = a.bloom_off[B], bo1 = a.bloom_off[B + 1];
+    if (atomicAdd(&C[B], 1u) == 0u) {
+        const uint32_t span = bo1 - bo0;
+        const uint32_t nseg = (span + kSeg - 1) / kSeg;
+        const uint32_t base = atomicAdd(&a.ctl->n_bseg[c3], nseg);
+        for (uint32_t s = 0; s < nseg; ++s) {
+            const uint32_t left = span - s * kSeg;
+            a.bseg[c3][base + s] =
+                make_uint4(B, bo0 + s * kSeg, (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u), bkB);
+        }
+    }
+}
+
+// Bloom phase, one pair slot (died stamp d, members pr) of a bloom with c
+// pairs killed this round and bloom number kB at round start.
+template <uint32_t kSeg>
+__device__ __forceinline__ void apply_slot(const PeelArgs &a, uint32_t d, uint2 pr, uint32_t c, uint32_t kB,
+                                           const Lvl &L, uint32_t np, uint32_t round,
+                                           unsigned long long &upd) {
+    if (d == kAlive) {
+        // a surviving pair: one butterfly lost per dead pair
+        decrement<kSeg>(a, pr.x, c, L, np, round + 1, false, 0, 0);
+        decrement<kSeg>(a, pr.y, c, L, np, round + 1, false, 0, 0);
+        upd += 2;
+    } else if (d == round && kB > 1u) {
+        // died now: a member outside S loses its k_B - 1 butterflies
+        const uint32_t sx = __ldcg(&a.state[pr.x]), sy = __ldcg(&a.state[pr.y]);
+        if (sx != round) {
+            decrement<kSeg>(a, pr.x, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+            ++upd;
+        }
+        if (sy != round) {
+            decrement<kSeg>(a, pr.y, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+            ++upd;
+        }
+    }
+}
+
 template <uint32_t kSeg>
 __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     constexpr uint32_t R = kSeg / 32;  // entries per lane
@@ -331,44 +379,57 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
         const uint32_t n_edges = ldcg_ui(&ctl->n_edges[par]);
         {
             const uint32_t n_items = ldcg_ui(&ctl->n_items[par]);
-            const bool spec = gwarp < a.item_cap;
-            uint4 it0 = spec ? __ldcg(&a.items[par][gwarp]) : make_uint4(0, 0, 0, 0);
             if (gtid == 0) ctl->n_bseg[(c3 + 1u) % 3u] = 0;
-            for (uint32_t i = gwarp; i < n_items; i += nwarps) {
-                const uint4 it = i == gwarp ? it0 : __ldcg(&a.items[par][i]);
+            for (uint32_t base = gwarp; base < n_items; base += nwarps * 32u) {
+                const uint32_t i = base + lane * nwarps;
+                const uint4 it = i < n_items ? __ldcg(&a.items[par][i]) : make_uint4(0, 0, 0, 0);
                 const uint32_t cnt = it.w & 0x7FFFFFFFu;
-                const uint64_t j0 = ((uint64_t)it.z << 32 | it.y) + lane;
-                uint32_t p[R], B[R];
-                bool won[R];
+                if (cnt <= kSmall) {
+                    // this lane's own item: its links' loads and stamps go out together
+                    const uint64_t j0 = (uint64_t)it.z << 32 | it.y;
+                    uint32_t p[kSmall], B[kSmall];
+                    bool won[kSmall];
 #pragma unroll
-                for (uint32_t r = 0; r < R; ++r) {
-                    const bool act = lane + 32u * r < cnt;
-                    p[r] = act ? a.inc[j0 + 32u * r] : 0u;
-                    won[r] = act;
-                }
-#pragma unroll
-                for (uint32_t r = 0; r < R; ++r)
-                    if (won[r]) B[r] = a.pair_bloom[p[r]];
-                // the first edge of S to stamp a pair kills it (once)
-#pragma unroll
-                for (uint32_t r = 0; r < R; ++r)
-                    if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
-#pragma unroll
-                for (uint32_t r = 0; r < R; ++r) {
-                    if (!won[r]) continue;
-                    const uint32_t bkB = ldcg_u32(&a.bk[B[r]]);
-                    const uint32_t bo0 = a.bloom_off[B[r]], bo1 = a.bloom_off[B[r] + 1];
-                    if (atomicAdd(&C[B[r]], 1u) == 0u) {
-                        const uint32_t span = bo1 - bo0;
-                        const uint32_t nseg = (span + kSeg - 1) / kSeg;
-                        const uint32_t base = atomicAdd(&ctl->n_bseg[c3], nseg);
-                        for (uint32_t s = 0; s < nseg; ++s) {
-                            const uint32_t left = span - s * kSeg;
-                            a.bseg[c3][base + s] = make_uint4(
-                                B[r], bo0 + s * kSeg,
-                                (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u), bkB);
-                        }
+                    for (uint32_t r = 0; r < kSmall; ++r) {
+                        won[r] = r < cnt;
+                        p[r] = won[r] ? a.inc[j0 + r] : 0u;
                     }
+#pragma unroll
+                    for (uint32_t r = 0; r < kSmall; ++r)
+                        if (won[r]) B[r] = a.pair_bloom[p[r]];
+                    // the first edge of S to stamp a pair kills it (once)
+#pragma unroll
+                    for (uint32_t r = 0; r < kSmall; ++r)
+                        if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
+#pragma unroll
+                    for (uint32_t r = 0; r < kSmall; ++r)
+                        if (won[r]) count_kill<kSeg>(a, C, B[r], c3);
+                }
+                // items with many links: the whole warp, one item at a time
+                unsigned big = __ballot_sync(0xffffffffu, cnt > kSmall);
+                while (big) {
+                    const int src = __ffs(big) - 1;
+                    big &= big - 1u;
+                    const uint32_t bcnt = __shfl_sync(0xffffffffu, cnt, src);
+                    const uint32_t jlo = __shfl_sync(0xffffffffu, it.y, src);
+                    const uint32_t jhi = __shfl_sync(0xffffffffu, it.z, src);
+                    const uint64_t j0 = ((uint64_t)jhi << 32 | jlo) + lane;
+                    uint32_t p[R], B[R];
+                    bool won[R];
+#pragma unroll
+                    for (uint32_t r = 0; r < R; ++r) {
+                        won[r] = lane + 32u * r < bcnt;
+                        p[r] = won[r] ? a.inc[j0 + 32u * r] : 0u;
+                    }
+#pragma unroll
+                    for (uint32_t r = 0; r < R; ++r)
+                        if (won[r]) B[r] = a.pair_bloom[p[r]];
+#pragma unroll
+                    for (uint32_t r = 0; r < R; ++r)
+                        if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
+#pragma unroll
+                    for (uint32_t r = 0; r < R; ++r)
+                        if (won[r]) count_kill<kSeg>(a, C, B[r], c3);
                 }
             }
         }
@@ -381,41 +442,43 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
         }
         {
             const uint32_t n_bseg = ldcg_ui(&ctl->n_bseg[c3]);
-            for (uint32_t i = gwarp; i < n_bseg; i += nwarps) {
-                const uint4 it = __ldcg(&a.bseg[c3][i]);
-                const uint32_t B = it.x, kB = it.w, cnt = it.z & 0x7FFFFFFFu;
-                const uint32_t c = ldcg_u32(&C[B]);
-                if ((it.z >> 31) && lane == 0) a.bk[B] = kB - c;
-                if (lane == 0) slots += cnt;
-                uint32_t d[R];
-                uint2 pr[R];
+            for (uint32_t base = gwarp; base < n_bseg; base += nwarps * 32u) {
+                const uint32_t i = base + lane * nwarps;
+                const uint4 it = i < n_bseg ? __ldcg(&a.bseg[c3][i]) : make_uint4(0, 0, 0, 0);
+                const uint32_t cnt = it.z & 0x7FFFFFFFu;
+                const uint32_t c = cnt ? __ldcg(&C[it.x]) : 0u;
+                if (cnt && (it.z >> 31)) a.bk[it.x] = it.w - c;
+                slots += cnt;
+                if (cnt <= kSmall) {
+                    uint32_t d[kSmall];
+                    uint2 pr[kSmall];
 #pragma unroll
-                for (uint32_t r = 0; r < R; ++r) {
-                    const bool act = lane + 32u * r < cnt;
-                    const uint32_t pp = it.y + lane + 32u * r;
-                    d[r] = act ? ldcg_u32(&a.died[pp]) : round + 1u;  // inactive: neither case below
-                    pr[r] = act ? a.pairs[pp] : make_uint2(0, 0);
-                }
-#pragma unroll
-                for (uint32_t r = 0; r < R; ++r) {
-                    if (d[r] == kAlive) {
-                        // a surviving pair: one butterfly lost per dead pair
-                        decrement<kSeg>(a, pr[r].x, c, L, np, round + 1, false, 0, 0);
-                        decrement<kSeg>(a, pr[r].y, c, L, np, round + 1, false, 0, 0);
-                        upd += 2;
-                    } else if (d[r] == round && kB > 1u) {
-                        // died now: a member outside S loses its k_B - 1 butterflies
-                        const uint32_t sx = ldcg_u32(&a.state[pr[r].x]);
-                        const uint32_t sy = ldcg_u32(&a.state[pr[r].y]);
-                        if (sx != round) {
-                            decrement<kSeg>(a, pr[r].x, (long long)kB - 1, L, np, round + 1, false, 0, 0);
-                            ++upd;
-                        }
-                        if (sy != round) {
-                            decrement<kSeg>(a, pr[r].y, (long long)kB - 1, L, np, round + 1, false, 0, 0);
-                            ++upd;
-                        }
+                    for (uint32_t r = 0; r < kSmall; ++r) {
+                        const bool act = r < cnt;
+                        d[r] = act ? __ldcg(&a.died[it.y + r]) : round + 1u;  // inactive: no case applies
+                        pr[r] = act ? a.pairs[it.y + r] : make_uint2(0, 0);
                     }
+#pragma unroll
+                    for (uint32_t r = 0; r < kSmall; ++r) apply_slot<kSeg>(a, d[r], pr[r], c, it.w, L, np, round, upd);
+                }
+                unsigned big = __ballot_sync(0xffffffffu, cnt > kSmall);
+                while (big) {
+                    const int src = __ffs(big) - 1;
+                    big &= big - 1u;
+                    const uint32_t bcnt = __shfl_sync(0xffffffffu, cnt, src);
+                    const uint32_t p0 = __shfl_sync(0xffffffffu, it.y, src) + lane;
+                    const uint32_t kB = __shfl_sync(0xffffffffu, it.w, src);
+                    const uint32_t bc = __shfl_sync(0xffffffffu, c, src);
+                    uint32_t d[R];
+                    uint2 pr[R];
+#pragma unroll
+                    for (uint32_t r = 0; r < R; ++r) {
+                        const bool act = lane + 32u * r < bcnt;
+                        d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : round + 1u;
+                        pr[r] = act ? a.pairs[p0 + 32u * r] : make_uint2(0, 0);
+                    }
+#pragma unroll
+                    for (uint32_t r = 0; r < R; ++r) apply_slot<kSeg>(a, d[r], pr[r], bc, kB, L, np, round, upd);
                 }
             }
             // clear C of the blooms the previous round touched (threads from
@@ -434,6 +497,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     }
     upd = dev::warp_sum(upd);
     if (lane == 0 && upd) atomicAdd(&ctl->updates, upd);
+    slots = dev::warp_sum(slots);
     if (lane == 0 && slots) atomicAdd(&ctl->slots, slots);
     if (gtid == 0) {
         ctl->rounds = round;
