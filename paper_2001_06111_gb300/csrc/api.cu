@@ -8,6 +8,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "bt_internal.cuh"
@@ -27,6 +28,8 @@ struct bt_handle {
     int count_nt = 512;   // schedule used by the next pipeline run
     int peel_seg = 32;
     std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (count_nt, peel_seg)
+    unsigned char *pinned = nullptr;  // page-locked staging for batch copies
+    size_t pinned_bytes = 0;
 };
 
 namespace {
@@ -253,6 +256,7 @@ int bt_destroy(bt_handle *h) {
     for (auto &ev : h->prof.ev)
         if (ev) cudaEventDestroy(ev);
     cudaFree(h->err_word);
+    if (h->pinned) cudaFreeHost(h->pinned);
     if (h->pool) cudaMemPoolDestroy(h->pool);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -454,6 +458,37 @@ int bt_profile_read(const bt_handle *h, bt_profile *out) {
     return BT_OK;
 }
 
+// Page-locked staging buffer of at least `bytes` (grown on demand), or null.
+static unsigned char *pinned_buffer(bt_handle *h, size_t bytes) {
+    if (h->pinned_bytes >= bytes) return h->pinned;
+    if (h->pinned) cudaFreeHost(h->pinned);
+    h->pinned = nullptr;
+    h->pinned_bytes = 0;
+    void *p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) return nullptr;
+    h->pinned = static_cast<unsigned char *>(p);
+    h->pinned_bytes = bytes;
+    return h->pinned;
+}
+
+// Runs fn(g) for g in [0, n) on up to 8 host threads.
+extern "C++" {
+template <typename F>
+static void parallel_for(uint32_t n, uint64_t total_bytes, F fn) {
+    unsigned nt = total_bytes > (64ull << 20) ? std::min(8u, std::max(1u, std::thread::hardware_concurrency())) : 1u;
+    if (nt <= 1 || n < 2) {
+        for (uint32_t g = 0; g < n; ++g) fn(g);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            for (uint32_t g = t; g < n; g += nt) fn(g);
+        });
+    for (auto &x : th) x.join();
+}
+}  // extern "C++"
+
 // Decomposes graphs[0..n) as one disjoint union (see bt_decompose_batch).
 static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uint32_t flags,
                            bt_batch_stats *acc, bt::Alloc &al) {
@@ -492,10 +527,20 @@ static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uin
         e = cudaMemcpyAsync(d_goff, goff.data(), 8 * (n + 1), cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_tab, tab.data(), 4 * tab.size(), cudaMemcpyHostToDevice, h->stream);
-        for (uint32_t g = 0; g < n && e == cudaSuccess; ++g)
-            if (graphs[g].m)
-                e = cudaMemcpyAsync(d_edges + 2 * goff[g], graphs[g].edges, 8 * graphs[g].m,
-                                    dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+        unsigned char *stage = dev ? nullptr : pinned_buffer(h, 12 * M + 16);
+        if (stage) {
+            // gather all host edge lists into page-locked memory, one DMA
+            parallel_for(n, 8 * M, [&](uint32_t g) {
+                if (graphs[g].m) memcpy(stage + 8 * goff[g], graphs[g].edges, 8 * graphs[g].m);
+            });
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_edges, stage, 8 * M, cudaMemcpyHostToDevice, h->stream);
+        } else {
+            for (uint32_t g = 0; g < n && e == cudaSuccess; ++g)
+                if (graphs[g].m)
+                    e = cudaMemcpyAsync(d_edges + 2 * goff[g], graphs[g].edges, 8 * graphs[g].m,
+                                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+        }
         if (e == cudaSuccess) e = cudaMemsetAsync(h->err_word, 0, sizeof(uint32_t), h->stream);
         uint32_t *bad = d_tab + 4 * (size_t)n;
         if (e == cudaSuccess)
@@ -523,12 +568,28 @@ static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uin
             rc = fail(h, pr.status, "peeling stopped: device barrier timeout or round limit");
     }
     if (rc == BT_OK) {
-        for (uint32_t g = 0; g < n && e == cudaSuccess; ++g) {
-            if (!graphs[g].m) continue;
-            if (graphs[g].support_out)
-                e = deliver(h, graphs[g].support_out, d_sup + goff[g], 8 * graphs[g].m, flags);
+        unsigned char *stage = (dev || M == 0) ? nullptr : pinned_buffer(h, 12 * M + 16);
+        if (stage) {
+            // one DMA of all results into page-locked memory, then scatter
+            e = cudaMemcpyAsync(stage, d_sup, 8 * M, cudaMemcpyDeviceToHost, h->stream);
             if (e == cudaSuccess)
-                e = deliver(h, graphs[g].phi_out, d_phi + goff[g], 4 * graphs[g].m, flags);
+                e = cudaMemcpyAsync(stage + 8 * M, d_phi, 4 * M, cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e == cudaSuccess)
+                parallel_for(n, 12 * M, [&](uint32_t g) {
+                    if (!graphs[g].m) return;
+                    if (graphs[g].support_out)
+                        memcpy(graphs[g].support_out, stage + 8 * goff[g], 8 * graphs[g].m);
+                    memcpy(graphs[g].phi_out, stage + 8 * M + 4 * goff[g], 4 * graphs[g].m);
+                });
+        } else {
+            for (uint32_t g = 0; g < n && e == cudaSuccess; ++g) {
+                if (!graphs[g].m) continue;
+                if (graphs[g].support_out)
+                    e = deliver(h, graphs[g].support_out, d_sup + goff[g], 8 * graphs[g].m, flags);
+                if (e == cudaSuccess)
+                    e = deliver(h, graphs[g].phi_out, d_phi + goff[g], 4 * graphs[g].m, flags);
+            }
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "returning batch results");
