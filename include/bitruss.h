@@ -256,6 +256,36 @@ typedef struct {
 int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const bt_tune *tune,
                        bt_batch_stats *stats, uint32_t flags);
 
+/* Statistics of a progressive-compression decomposition. */
+typedef struct {
+    uint64_t passes;           /* candidate subgraphs peeled (eps values with unassigned edges) */
+    uint64_t rounds, levels;   /* peeling rounds and levels, summed over passes */
+    uint64_t support_updates;  /* support decrements applied, summed over passes */
+    uint64_t candidate_edges;  /* edges of the candidate subgraphs, summed */
+    uint64_t wedges;           /* priority-obeyed wedges of the candidate subgraphs, summed */
+    uint64_t k_max;            /* largest k with >= k edges of support >= k */
+    uint64_t alpha;            /* eps step, ceil(k_max * tau) */
+} bt_pc_stats;
+
+/*
+ * Bitruss numbers by progressive compression (BiT-PC, Section V-C, Alg. 7):
+ * after counting, eps runs from k_max down to 0 in steps of
+ * alpha = ceil(k_max * tau).  For each eps the candidate subgraph G_{>=eps}
+ * (edges of support >= eps, which holds every k-bitruss with k >= eps,
+ * Lemma 10) gets a compressed BE-Index (Alg. 6: blooms keep all their twin
+ * pairs, edges already assigned get no links and receive no updates) and is
+ * peeled in batches; edges leaving at a level >= eps are assigned, the others
+ * wait for a smaller eps.  Every edge below eps is taken in one batch level
+ * eps - 1, so a pass spends one level on them.  Same results as bt_decompose
+ * (Thm. 3); fewer support updates on graphs with hub edges.
+ *   tau in (0, 1] (the paper uses 0.02 by default and suggests 0.05-0.2).
+ *   support_out may be NULL; stats may be NULL.
+ * Errors: as bt_decompose, plus BT_ERR_ARG for tau outside (0, 1].
+ */
+int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                             double tau, uint64_t *support_out, uint32_t *phi_out, bt_pc_stats *stats,
+                             uint32_t flags);
+
 /* ---------------------------------------------------------------- serving
  * A request loop with continuous batching.  Each submitted request is one
  * graph (host pointers, as in bt_graph; the caller keeps edges and outputs

@@ -34,7 +34,7 @@ EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_
             "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
             "bt_profile_read", "bt_count_support_static", "bt_decompose_batch",
             "bt_server_create", "bt_server_destroy", "bt_server_submit", "bt_server_poll",
-            "bt_server_stats_read")
+            "bt_server_stats_read", "bt_decompose_progressive")
 
 
 class BitrussError(RuntimeError):
@@ -89,6 +89,13 @@ class BatchStats(ctypes.Structure):
                 ("support_updates", ctypes.c_uint64), ("count_threads", ctypes.c_uint32),
                 ("peel_item", ctypes.c_uint32), ("tuned", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+class PcStats(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("levels", ctypes.c_uint64), ("support_updates", ctypes.c_uint64),
+                ("candidate_edges", ctypes.c_uint64), ("wedges", ctypes.c_uint64),
+                ("k_max", ctypes.c_uint64), ("alpha", ctypes.c_uint64)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -154,6 +161,8 @@ def load(path: str = LIB_PATH):
         lib.bt_server_submit.argtypes = [P, ctypes.POINTER(Graph), ctypes.POINTER(U64)]
         lib.bt_server_poll.argtypes = [P, U64, I, ctypes.POINTER(RequestInfo)]
         lib.bt_server_stats_read.argtypes = [P, ctypes.POINTER(ServerStats)]
+        lib.bt_decompose_progressive.argtypes = [P, P, U64, U32, U32, ctypes.c_double, P, P,
+                                                 ctypes.POINTER(PcStats), U32]
         lib.bt_profile_enable.argtypes = [P, I]
         lib.bt_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         lib.bt_estimate_bytes.argtypes = [P, U64, U32, U32, U32, ctypes.POINTER(U64),
@@ -386,6 +395,21 @@ def bt_profile_read(h: Handle) -> dict:
     p = Profile()
     _check(h, load().bt_profile_read(h.ptr, ctypes.byref(p)))
     return _as_dict(p)
+
+
+def bt_decompose_progressive(h: Handle, edges, nU: int, nL: int, tau: float = 0.1,
+                             support_out=None, phi_out=None, flags: int = 0, want_support: bool = True):
+    """Progressive compression (BiT-PC); returns (support or None, phi, stats)."""
+    ptr, m, f, keep = _edges_arg(edges)
+    dev = keep if f & BT_DEVICE_PTRS else None
+    sup, sptr = (None, None)
+    if want_support or support_out is not None:
+        sup, sptr = _out(dev, m, np.uint64, _torch_dtype("uint64"), support_out)
+    phi, pptr = _out(dev, m, np.uint32, _torch_dtype("uint32"), phi_out)
+    st = PcStats()
+    _check(h, load().bt_decompose_progressive(h.ptr, ptr, m, nU, nL, tau, sptr, pptr,
+                                              ctypes.byref(st), flags | f))
+    return sup, phi, _as_dict(st)
 
 
 def bt_estimate_bytes(edges, nU: int, nL: int, flags: int = 0):

@@ -2,6 +2,7 @@
 // host/device staging, the handle's stream and memory pool, and the call
 // sequences CSR build -> wedge count -> BE-Index emit -> batch peel.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -159,9 +160,11 @@ cudaError_t deliver(bt_handle *h, void *dst, const void *src, size_t bytes, uint
 
 // Count (+ optional index).  d_support receives supports (device).
 int count_and_index(bt_handle *h, Prepared &P, uint64_t *d_support, bool want_index,
-                    bt::Index &ix, uint64_t &butterflies, bt::Alloc &al) {
+                    bt::Index &ix, uint64_t &butterflies, bt::Alloc &al,
+                    const uint8_t *assigned = nullptr) {
     bt::CountOut co;
     co.support = d_support;
+    co.assigned = assigned;
     uint64_t W = 0;
     if (want_index) {
         co.inc_cnt = al.get<uint32_t>(P.g.m);
@@ -750,6 +753,134 @@ int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const b
         h->last.support_updates = acc.support_updates;
     }
     if (stats && rc == BT_OK) *stats = acc;
+    return rc;
+}
+
+int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                             double tau, uint64_t *support_out, uint32_t *phi_out, bt_pc_stats *stats,
+                             uint32_t flags) {
+    int rc = check_args(h, edges, m, nU, nL, flags);
+    if (rc) return rc;
+    h->err.clear();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (!(tau > 0.0 && tau <= 1.0)) return fail(h, BT_ERR_ARG, "tau must be in (0, 1]");
+    if (m == 0) return BT_OK;
+    if (!phi_out) return fail(h, BT_ERR_ARG, "phi_out is NULL");
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    call_begin(h, al, m, nU + nL);
+    const bool dev = flags & BT_DEVICE_PTRS;
+    bt_pc_stats st{};
+    Prepared P;
+    rc = prepare(h, edges, m, nU, nL, flags, P, al);
+    uint64_t *d_sup0 = (dev && support_out) ? support_out : al.get<uint64_t>(m);
+    uint32_t *d_phi = dev ? phi_out : al.get<uint32_t>(m);
+    uint8_t *d_asg = al.get<uint8_t>(m);
+    int32_t *cand = al.get<int32_t>(2 * m);
+    uint32_t *cmap = al.get<uint32_t>(m);
+    uint8_t *cass = al.get<uint8_t>(m);
+    uint32_t *phi_local = al.get<uint32_t>(m);
+    uint64_t *sup_c = al.get<uint64_t>(m);
+    uint32_t *hist = al.get<uint32_t>(m + 1);
+    unsigned long long *counts = al.get<unsigned long long>(2);
+    if (rc == BT_OK && al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating");
+    uint64_t bf = 0;
+    bt::Index unused;
+    // supports of G (the counting process of Alg. 7)
+    if (rc == BT_OK) rc = count_and_index(h, P, d_sup0, false, unused, bf, al);
+    bt::free_csr(P.g, al);
+    // k_max: the largest k with at least k edges of support >= k (Section V-C)
+    uint64_t kmax = 0;
+    cudaError_t e = cudaSuccess;
+    if (rc == BT_OK) {
+        std::vector<uint32_t> hh(m + 1);
+        e = bt::support_hist(d_sup0, m, hist, al);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hh.data(), hist, 4 * (m + 1), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_asg, 0, m, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "computing k_max");
+        uint64_t acc = 0;
+        for (uint64_t k = m + 1; k-- > 0;) {
+            acc += hh[k];
+            if (acc >= k) {
+                kmax = k;
+                break;
+            }
+        }
+    }
+    const uint64_t alpha = std::max<uint64_t>(1, (uint64_t)std::ceil((double)kmax * tau));
+    st.k_max = kmax;
+    st.alpha = alpha;
+    uint64_t eps = kmax;
+    while (rc == BT_OK) {
+        // candidate subgraph G_{>=eps} (Alg. 7, extraction step)
+        unsigned long long hc[2] = {0, 0};
+        e = bt::select_candidates(P.d_edges, d_sup0, m, eps, d_asg, cand, cmap, cass, counts, al);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(h, e, "extracting a candidate subgraph");
+            break;
+        }
+        if (hc[1] > 0) {
+            // compressed BE-Index of the candidate graph (Alg. 6), then a batch
+            // peel that settles every edge leaving at a level >= eps
+            Prepared Q;
+            rc = prepare(h, cand, hc[0], nU, nL, (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, Q, al);
+            bt::Index ix;
+            if (rc == BT_OK) rc = count_and_index(h, Q, sup_c, true, ix, bf, al, cass);
+            bt::free_csr(Q.g, al);
+            bt::PeelResult pr;
+            if (rc == BT_OK) {
+                bt::PeelOpts o;
+                o.assigned = cass;
+                o.m_active = hc[1];
+                o.k_init = eps > 0 ? (long long)eps - 1 : 0;
+                o.assign_from = (long long)eps;
+                e = cudaMemsetAsync(phi_local, 0xFF, 4 * hc[0], h->stream);
+                if (e == cudaSuccess) e = bt::peel(ix, sup_c, phi_local, pr, h->num_sms, al, h->peel_seg, &o);
+                if (e == cudaSuccess) e = bt::settle(cmap, hc[0], cass, phi_local, d_phi, d_asg, al);
+                if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling a candidate subgraph");
+                else if (pr.status == BT_ERR_OVERFLOW) rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
+                else if (pr.status != BT_OK) rc = fail(h, pr.status, "peeling stopped: device barrier timeout or round limit");
+            }
+            st.wedges += ix.w;
+            bt::free_index(ix, al);
+            st.passes++;
+            st.rounds += pr.rounds;
+            st.levels += pr.levels;
+            st.support_updates += pr.updates;
+            st.candidate_edges += hc[0];
+        }
+        if (eps == 0) break;
+        eps = eps > alpha ? eps - alpha : 0;
+    }
+    if (rc == BT_OK) {
+        e = cudaSuccess;
+        if (support_out) e = deliver(h, support_out, d_sup0, sizeof(uint64_t) * m, flags);
+        if (e == cudaSuccess) e = deliver(h, phi_out, d_phi, sizeof(uint32_t) * m, flags);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "returning results");
+    }
+    al.put(P.owned);
+    if (!(dev && support_out)) al.put(d_sup0);
+    if (!dev) al.put(d_phi);
+    al.put(d_asg);
+    al.put(cand);
+    al.put(cmap);
+    al.put(cass);
+    al.put(phi_local);
+    al.put(sup_c);
+    al.put(hist);
+    al.put(counts);
+    call_end(h, al);
+    if (rc == BT_OK) {
+        h->last.rounds = st.rounds;
+        h->last.levels = st.levels;
+        h->last.support_updates = st.support_updates;
+        if (stats) *stats = st;
+    }
+    cudaStreamSynchronize(h->stream);
     return rc;
 }
 

@@ -117,6 +117,9 @@ struct CountOut {
     uint64_t *w2v = nullptr;      // [n] bloom wedges per start vertex (index mode)
     uint64_t *nbv = nullptr;      // [n] blooms per start vertex (index mode)
     unsigned long long *butterflies_dev = nullptr;  // [1] set by count_wedges; caller frees
+    // [m] or nullptr: edges whose bitruss number is already known (progressive
+    // compression); they get no links and are flagged in bit 31 inside pairs
+    const uint8_t *assigned = nullptr;
 };
 // nt: count block size (256, 512 or 1024; anything else means 512)
 cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt = 512);
@@ -148,9 +151,32 @@ struct PeelResult {
     int status = BT_OK;
 };
 // support: [m] initial supports (device, preserved); phi_out: [m] device.
+// Progressive compression (Alg. 6-7): edges with assigned[e] set keep their
+// phi and are never peeled; the m_active others are peeled starting at level
+// k_init, and phi is written only for edges leaving at a level >= assign_from.
+struct PeelOpts {
+    const uint8_t *assigned = nullptr;
+    uint64_t m_active = 0;
+    long long k_init = 0;
+    long long assign_from = 0;
+};
 // seg: peel work-item size (32 or 64 entries; anything else means 32)
 cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
-                 int num_sms, Alloc &al, int seg = 32);
+                 int num_sms, Alloc &al, int seg = 32, const PeelOpts *opts = nullptr);
+
+// ---------------------------------------------------------------- progressive compression
+// hist[min(sup, m)] counts over all edges (m + 1 bins, zeroed here).
+cudaError_t support_hist(const uint64_t *sup, uint64_t m, uint32_t *hist, Alloc &al);
+// Candidate subgraph G_{>=eps}: edges with support >= eps, compacted (cand
+// int32 pairs, cmap = global edge id, cassigned = assigned flag);
+// counts[0] = candidates, counts[1] = unassigned candidates.
+cudaError_t select_candidates(const int32_t *edges, const uint64_t *sup, uint64_t m, uint64_t eps,
+                              const uint8_t *assigned, int32_t *cand, uint32_t *cmap,
+                              uint8_t *cassigned, unsigned long long *counts, Alloc &al);
+// Copies the phi a pass settled (phi_local != 0xFFFFFFFF, edge not yet
+// assigned) to the global arrays and marks those edges assigned.
+cudaError_t settle(const uint32_t *cmap, uint64_t n, const uint8_t *cassigned,
+                   const uint32_t *phi_local, uint32_t *phi, uint8_t *assigned, Alloc &al);
 
 // ---------------------------------------------------------------- helpers
 __host__ __device__ inline int bits_for(uint64_t maxval) {

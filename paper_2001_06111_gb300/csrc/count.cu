@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(NT) k_count(
     const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
     const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
     uint32_t *cnt_all, unsigned long long *support, uint32_t *inc_cnt, uint64_t *w2v,
-    uint64_t *nbv, unsigned long long *totals, uint32_t *queue) {
+    uint64_t *nbv, unsigned long long *totals, uint32_t *queue, const uint8_t *__restrict__ assigned) {
     __shared__ Chunk<NT> ch;
     __shared__ unsigned long long s_acc[NT];
     __shared__ uint32_t s_inc[NT];
@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(NT) k_count(
                     atomicAdd(&support[evw], (unsigned long long)(c - 1));
                     atomicAdd(&s_acc[vi], (unsigned long long)(c - 1));
                     if (kIndex) {
-                        atomicAdd(&inc_cnt[evw], 1u);
-                        atomicAdd(&s_inc[vi], 1u);
+                        // edges already assigned (progressive compression) get no links
+                        if (!assigned || !assigned[evw]) atomicAdd(&inc_cnt[evw], 1u);
+                        if (!assigned || !assigned[ch.e[vi]]) atomicAdd(&s_inc[vi], 1u);
                         ++w2_local;
                     }
                 }
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(NT) k_emit(
     uint32_t *cnt_all, uint32_t *aux_all, const uint64_t *__restrict__ bloom_base,
     const uint64_t *__restrict__ pair_base, const uint64_t *__restrict__ inc_off,
     uint32_t *inc_fill, uint32_t *bloom_k, uint32_t *bloom_off, uint2 *pairs,
-    uint32_t *pair_bloom, uint32_t *inc, uint32_t *queue) {
+    uint32_t *pair_bloom, uint32_t *inc, uint32_t *queue, const uint8_t *__restrict__ assigned) {
     __shared__ Chunk<NT> ch;
     __shared__ uint32_t s_q;
     // bloom count (high 32 bits) and pair count (low 32 bits) of the vertex,
@@ -237,12 +238,18 @@ __global__ void __launch_bounds__(NT) k_emit(
                     uint32_t pos = atomicSub(&cnt[w], 1u) - 1u;
                     uint32_t slot = ld_cg(&bloom_off[B]) + pos;
                     uint32_t euv = ch.e[vi], evw = eid[arc];
-                    pairs[slot] = make_uint2(euv, evw);
+                    const bool fu = assigned && assigned[euv], fw = assigned && assigned[evw];
+                    // an assigned edge is flagged in bit 31 and gets no link
+                    pairs[slot] = make_uint2(euv | (fu ? 0x80000000u : 0u), evw | (fw ? 0x80000000u : 0u));
                     pair_bloom[slot] = (uint32_t)B;
-                    uint32_t q1 = atomicAdd(&inc_fill[euv], 1u);
-                    inc[inc_off[euv] + q1] = slot;
-                    uint32_t q2 = atomicAdd(&inc_fill[evw], 1u);
-                    inc[inc_off[evw] + q2] = slot;
+                    if (!fu) {
+                        uint32_t q1 = atomicAdd(&inc_fill[euv], 1u);
+                        inc[inc_off[euv] + q1] = slot;
+                    }
+                    if (!fw) {
+                        uint32_t q2 = atomicAdd(&inc_fill[evw], 1u);
+                        inc[inc_off[evw] + q2] = slot;
+                    }
                 }
             }
             __syncthreads();
@@ -279,10 +286,10 @@ void launch_count(bool index, unsigned blocks, const Csr &g, uint32_t *cnt, unsi
                   CountOut &o, unsigned long long *totals, uint32_t *queue, cudaStream_t st) {
     if (index)
         k_count<true, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, cnt, sup,
-                                                  o.inc_cnt, o.w2v, o.nbv, totals, queue);
+                                                  o.inc_cnt, o.w2v, o.nbv, totals, queue, o.assigned);
     else
         k_count<false, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, cnt, sup,
-                                                   nullptr, nullptr, nullptr, totals, queue);
+                                                   nullptr, nullptr, nullptr, totals, queue, nullptr);
 }
 
 }  // namespace
@@ -368,7 +375,7 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     al.mark(kPhEmit, false);
 #define BT_EMIT_ARGS                                                                         \
     g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, cnt, aux, bloom_base, pair_base, ix.inc_off,  \
-        inc_fill, ix.bloom_k, ix.bloom_off, ix.pairs, ix.pair_bloom, ix.inc, queue
+        inc_fill, ix.bloom_k, ix.bloom_off, ix.pairs, ix.pair_bloom, ix.inc, queue, c.assigned
     if (nt == 256) k_emit<256><<<blocks, 256, 0, al.stream>>>(BT_EMIT_ARGS);
     else if (nt == 1024) k_emit<1024><<<blocks, 1024, 0, al.stream>>>(BT_EMIT_ARGS);
     else k_emit<512><<<blocks, 512, 0, al.stream>>>(BT_EMIT_ARGS);

@@ -93,6 +93,11 @@ struct PeelArgs {
     uint64_t item_cap;
     Ctl *ctl;
     uint64_t round_limit;
+    // progressive compression: peel only the m_active unassigned edges, start
+    // at level k_init, and record phi only for levels >= assign_from
+    uint64_t m_active;
+    long long k_init;
+    long long assign_from;
 };
 
 // Loop state every thread keeps identically (derived from values read after
@@ -163,7 +168,7 @@ template <uint32_t kSeg>
 __device__ __forceinline__ void push_edge(const PeelArgs &a, uint32_t e, uint32_t dst,
                                           uint32_t next_round, uint64_t ib, uint64_t ie, long long k) {
     a.state[e] = next_round;
-    a.phi[e] = (uint32_t)k;  // e leaves in a batch of this level
+    if (k >= a.assign_from) a.phi[e] = (uint32_t)k;  // e leaves in a batch of this level
     const uint64_t d = ie - ib;
     const uint32_t nseg = d == 0 ? 1u : (uint32_t)((d + kSeg - 1) / kSeg);
     const uint32_t base = atomicAdd(&a.ctl->n_items[dst], nseg);
@@ -230,20 +235,25 @@ template <uint32_t kSeg>
 __device__ __forceinline__ void apply_slot(const PeelArgs &a, uint32_t d, uint2 pr, uint32_t c, uint32_t kB,
                                            const Lvl &L, uint32_t np, uint32_t round,
                                            unsigned long long &upd) {
+    // bit 31 flags an edge whose bitruss number is already known: it is never
+    // peeled again, so it needs no decrement
+    const bool fx = pr.x >> 31, fy = pr.y >> 31;
+    const uint32_t ex = pr.x & 0x7FFFFFFFu, ey = pr.y & 0x7FFFFFFFu;
     if (d == kAlive) {
         // a surviving pair: one butterfly lost per dead pair
-        decrement<kSeg>(a, pr.x, c, L, np, round + 1, false, 0, 0);
-        decrement<kSeg>(a, pr.y, c, L, np, round + 1, false, 0, 0);
-        upd += 2;
+        if (!fx) decrement<kSeg>(a, ex, c, L, np, round + 1, false, 0, 0);
+        if (!fy) decrement<kSeg>(a, ey, c, L, np, round + 1, false, 0, 0);
+        upd += (fx ? 0 : 1) + (fy ? 0 : 1);
     } else if (d == round && kB > 1u) {
         // died now: a member outside S loses its k_B - 1 butterflies
-        const uint32_t sx = __ldcg(&a.state[pr.x]), sy = __ldcg(&a.state[pr.y]);
+        const uint32_t sx = fx ? round : __ldcg(&a.state[ex]);
+        const uint32_t sy = fy ? round : __ldcg(&a.state[ey]);
         if (sx != round) {
-            decrement<kSeg>(a, pr.x, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+            decrement<kSeg>(a, ex, (long long)kB - 1, L, np, round + 1, false, 0, 0);
             ++upd;
         }
         if (sy != round) {
-            decrement<kSeg>(a, pr.y, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+            decrement<kSeg>(a, ey, (long long)kB - 1, L, np, round + 1, false, 0, 0);
             ++upd;
         }
     }
@@ -258,9 +268,9 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t nthreads = gridDim.x * blockDim.x;
     Ctl *ctl = a.ctl;
-    uint64_t remaining = a.m;
+    uint64_t remaining = a.m_active;
     uint32_t round = 0;
-    Lvl L{0, 0, 0};
+    Lvl L{a.k_init, 0, 0};
     uint32_t ap = 0;  // current alive list
     bool level_jump = true;
     unsigned long long upd = 0, slots = 0;
@@ -505,12 +515,16 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     }
 }
 
+// Edges already assigned (mask set) start in the permanent state: never alive,
+// never queued.
+constexpr uint32_t kPerm = 0xFFFFFFFEu;
 __global__ void k_peel_init(const uint64_t *support, uint64_t m, long long *sup, uint32_t *state,
+                            const uint8_t *assigned,
                             uint32_t *alive) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
         sup[i] = (long long)support[i];
-        state[i] = kAlive;
+        state[i] = (assigned && assigned[i]) ? kPerm : kAlive;
         alive[i] = (uint32_t)i;
     }
 }
@@ -524,11 +538,11 @@ inline unsigned grid_for(uint64_t items, int threads, unsigned cap) {
 }  // namespace
 
 cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
-                 int num_sms, Alloc &al, int seg) {
+                 int num_sms, Alloc &al, int seg, const PeelOpts *opts) {
     const uint32_t kSeg = seg == 64 ? 64u : 32u;
     const uint64_t m = ix.m;
     res = PeelResult{};
-    if (m == 0) return cudaSuccess;
+    if (m == 0 || (opts && opts->assigned && opts->m_active == 0)) return cudaSuccess;
     const uint64_t item_cap = m + (2 * ix.w2) / kSeg + 2;
     const uint64_t bseg_cap = ix.nb + ix.w2 / kSeg + 2;
     PeelArgs a{};
@@ -555,11 +569,14 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     a.item_cap = item_cap;
     a.ctl = al.get<Ctl>(1);
     a.round_limit = m + 1;
+    a.m_active = (opts && opts->assigned) ? opts->m_active : m;
+    a.k_init = opts ? opts->k_init : 0;
+    a.assign_from = opts ? opts->assign_from : 0;
     if (al.err != cudaSuccess) return al.err;
     cudaStream_t st = al.stream;
     al.mark(kPhPeel, false);
-    k_peel_init<<<grid_for(m, 256, (unsigned)num_sms * 16), 256, 0, st>>>(support, m, a.sup, a.state,
-                                                                          a.alive[0]);
+    k_peel_init<<<grid_for(m, 256, (unsigned)num_sms * 16), 256, 0, st>>>(
+        support, m, a.sup, a.state, opts ? opts->assigned : nullptr, a.alive[0]);
     al.launches++;
     BT_CUDA(cudaMemsetAsync(a.died, 0xFF, sizeof(uint32_t) * (ix.w2 ? ix.w2 : 1), st));
     if (ix.nb) {
