@@ -205,9 +205,12 @@ __device__ __forceinline__ void decrement(const PeelArgs &a, uint32_t e, long lo
     if (old >= L.khi && now < L.khi) push_near(a, e, L.nq);
 }
 
+// Window above the current minimum: narrow enough that a level jump scans few
+// edges at high levels (dense cores hold many edges in a support range), wide
+// enough that rebuilds from the full alive list stay rare.
 __device__ __forceinline__ long long window_top(long long kmin) {
-    long long w = kmin / 4;
-    return kmin + (w < 16 ? 16 : w);
+    long long w = kmin / 64;
+    return kmin + (w < 8 ? 8 : w);
 }
 
 // Incidence phase, one killed pair of bloom B: count it in C(B) and, for the
