@@ -111,6 +111,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world_size: int, units_per_rank: int, steps: int, total_ms: float) -> float:
+    """Whole-job units per second: every rank processed its own replica."""
+    return world_size * units_per_rank * steps / (total_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -423,12 +438,8 @@ def main():
         dist.barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * m * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), dist)
+    value = job_throughput(ws, m, args.steps, total_ms)
 
     # end-to-end through the C ABI with host buffers
     e2e_steps = max(3, args.steps // 2)
@@ -437,8 +448,8 @@ def main():
     for _ in range(e2e_steps):
         sup_h, phi_h, _ = bt.bt_decompose(h, g.edges, g.nU, g.nL)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = ws * m * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_value = job_throughput(ws, m, e2e_steps, e2e_s * 1e3)
 
     if rank != 0:
         if dist:
