@@ -146,7 +146,9 @@ def algorithmic_bytes(p):
 
 def measured_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or
-    None when there is none or the kernel source changed since the capture."""
+    None when there is none or a source it lists (the kernel's own file, and
+    the CSR build that numbers the edges the kernel walks) changed since the
+    capture."""
     import hashlib
     import re
     src = {"peel": "peel.cu", "count": "count.cu", "emit": "count.cu"}.get(kernel)
@@ -155,12 +157,13 @@ def measured_traffic(kernel: str, workload: str):
         return None
     text = open(prof).read()
     m_t = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
-    m_h = re.search(r"sha256 \(csrc/[a-z_.]+\) \| ([0-9a-f]{64})", text)
-    if not m_t or not m_h:
+    hashes = dict(re.findall(r"sha256 \(csrc/([a-z_.]+)\) \| ([0-9a-f]{64})", text))
+    if not m_t or src not in hashes or "csr.cu" not in hashes:
         return None
-    with open(os.path.join(ROOT, "paper_2001_06111_gb300", "csrc", src), "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != m_h.group(1):
-            return None
+    for name, digest in hashes.items():
+        with open(os.path.join(ROOT, "paper_2001_06111_gb300", "csrc", name), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return None
     return int(m_t.group(1))
 
 

@@ -158,7 +158,9 @@ cudaError_t deliver(bt_handle *h, void *dst, const void *src, size_t bytes, uint
                            h->stream);
 }
 
-// Count (+ optional index).  d_support receives supports (device).
+// Count (+ optional index).  d_support receives supports (device) indexed by
+// internal edge id (P.g.newid maps input ids to them; with an index, the map
+// moves to ix.newid).
 int count_and_index(bt_handle *h, Prepared &P, uint64_t *d_support, bool want_index,
                     bt::Index &ix, uint64_t &butterflies, bt::Alloc &al,
                     const uint8_t *assigned = nullptr) {
@@ -201,6 +203,8 @@ int count_and_index(bt_handle *h, Prepared &P, uint64_t *d_support, bool want_in
         if (e != cudaSuccess) return cuda_fail(h, e, "emitting the BE-Index");
         ix.w = W;
         ix.butterflies = bf;
+        ix.newid = P.g.newid;  // the index speaks internal edge ids
+        P.g.newid = nullptr;
     }
     return BT_OK;
 }
@@ -280,19 +284,22 @@ int bt_count_support(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU
     call_begin(h, al, m, nU + nL);
     Prepared P;
     rc = prepare(h, edges, m, nU, nL, flags, P, al);
-    uint64_t *d_sup = nullptr;
+    uint64_t *d_sup = nullptr, *d_int = nullptr;
     if (rc == BT_OK) {
+        d_int = al.get<uint64_t>(m);
         d_sup = (flags & BT_DEVICE_PTRS) ? support_out : al.get<uint64_t>(m);
-        if (!d_sup) rc = cuda_fail(h, al.err, "allocating supports");
+        if (al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating supports");
     }
     bt::Index unused;
     uint64_t bf = 0;
-    if (rc == BT_OK) rc = count_and_index(h, P, d_sup, false, unused, bf, al);
+    if (rc == BT_OK) rc = count_and_index(h, P, d_int, false, unused, bf, al);
     if (rc == BT_OK) {
-        cudaError_t e = deliver(h, support_out, d_sup, sizeof(uint64_t) * m, flags);
+        cudaError_t e = bt::gather_u64(d_int, P.g.newid, d_sup, m, al);  // back to input order
+        if (e == cudaSuccess) e = deliver(h, support_out, d_sup, sizeof(uint64_t) * m, flags);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "returning supports");
     }
+    al.put(d_int);
     if (!(flags & BT_DEVICE_PTRS)) al.put(d_sup);
     release(P, al);
     call_end(h, al);
@@ -373,14 +380,26 @@ int bt_index_export(bt_handle *h, bt_bloom_rec *blooms_out, uint32_t *pairs_out,
         if (e == cudaSuccess)
             for (uint64_t i = 0; i < ix.nb; ++i) blooms_out[i] = bt_bloom_rec{k[i], off[i]};
     }
-    if (e == cudaSuccess && pairs_out && ix.w2)
+    // the index holds internal edge ids: map them back to input ids
+    std::vector<uint32_t> newid(ix.m), orig(ix.m);
+    if (e == cudaSuccess && ix.m && (pairs_out || edge_deg_out)) {
+        e = cudaMemcpyAsync(newid.data(), ix.newid, 4 * ix.m, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        for (uint64_t i = 0; i < ix.m; ++i) orig[newid[i]] = (uint32_t)i;
+    }
+    if (e == cudaSuccess && pairs_out && ix.w2) {
         e = cudaMemcpyAsync(pairs_out, ix.pairs, 8 * ix.w2, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess)
+            for (uint64_t i = 0; i < 2 * ix.w2; ++i) pairs_out[i] = orig[pairs_out[i] & 0x7FFFFFFFu];
+    }
     if (e == cudaSuccess && edge_deg_out && ix.m) {
         std::vector<uint64_t> off(ix.m + 1);
         e = cudaMemcpyAsync(off.data(), ix.inc_off, 8 * (ix.m + 1), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e == cudaSuccess)
-            for (uint64_t i = 0; i < ix.m; ++i) edge_deg_out[i] = (uint32_t)(off[i + 1] - off[i]);
+            for (uint64_t i = 0; i < ix.m; ++i)
+                edge_deg_out[i] = (uint32_t)(off[newid[i] + 1] - off[newid[i]]);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "exporting the index");
@@ -401,11 +420,15 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
     const bool dev = flags & BT_DEVICE_PTRS;
     uint64_t *d_sup = (dev && support_out) ? support_out : al.get<uint64_t>(m);
     uint32_t *d_phi = dev ? phi_out : al.get<uint32_t>(m);
+    uint64_t *s_int = al.get<uint64_t>(m);  // internal edge order
+    uint32_t *p_int = al.get<uint32_t>(m);
     if (al.err != cudaSuccess) return cuda_fail(h, al.err, "allocating outputs");
-    rc = build_index_impl(h, edges, m, nU, nL, flags, d_sup, al);
+    rc = build_index_impl(h, edges, m, nU, nL, flags, s_int, al);
     bt::PeelResult pr;
     if (rc == BT_OK) {
-        cudaError_t e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al, h->peel_seg);
+        cudaError_t e = bt::peel(h->index, s_int, p_int, pr, h->num_sms, al, h->peel_seg);
+        if (e == cudaSuccess) e = bt::gather_u64(s_int, h->index.newid, d_sup, m, al);
+        if (e == cudaSuccess) e = bt::gather_u32(p_int, h->index.newid, d_phi, m, al);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
         else if (pr.status == BT_ERR_OVERFLOW)
             rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
@@ -427,6 +450,8 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
     }
     if (!(dev && support_out)) al.put(d_sup);
     if (!dev) al.put(d_phi);
+    al.put(s_int);
+    al.put(p_int);
     call_end(h, al);
     if (rc == BT_OK) {
         h->last.n_wedges = h->index.w;
@@ -564,6 +589,20 @@ static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uin
     bt::PeelResult pr;
     if (rc == BT_OK && M > 0) {
         e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al, h->peel_seg);
+        // results back to input order (the edge array is free by now: reuse it)
+        uint64_t *g_sup = reinterpret_cast<uint64_t *>(d_edges);
+        uint32_t *g_phi = al.get<uint32_t>(M);
+        if (e == cudaSuccess && !g_phi) e = al.err;
+        if (e == cudaSuccess) e = bt::gather_u64(d_sup, h->index.newid, g_sup, M, al);
+        if (e == cudaSuccess) e = bt::gather_u32(d_phi, h->index.newid, g_phi, M, al);
+        if (e == cudaSuccess) {
+            d_edges = reinterpret_cast<int32_t *>(d_sup);  // freed below under its old name
+            d_sup = g_sup;
+            al.put(d_phi);
+            d_phi = g_phi;
+        } else {
+            al.put(g_phi);
+        }
         if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
         else if (pr.status == BT_ERR_OVERFLOW)
             rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
@@ -783,11 +822,17 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
     uint64_t *sup_c = al.get<uint64_t>(m);
     uint32_t *hist = al.get<uint32_t>(m + 1);
     unsigned long long *counts = al.get<unsigned long long>(2);
+    uint8_t *cass_int = al.get<uint8_t>(m);   // candidate flags in internal edge order
+    uint32_t *phi_c = al.get<uint32_t>(m);    // candidate phi in candidate input order
     if (rc == BT_OK && al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating");
     uint64_t bf = 0;
     bt::Index unused;
     // supports of G (the counting process of Alg. 7)
-    if (rc == BT_OK) rc = count_and_index(h, P, d_sup0, false, unused, bf, al);
+    if (rc == BT_OK) rc = count_and_index(h, P, sup_c, false, unused, bf, al);
+    if (rc == BT_OK) {
+        cudaError_t eg = bt::gather_u64(sup_c, P.g.newid, d_sup0, m, al);  // input order
+        if (eg != cudaSuccess) rc = cuda_fail(h, eg, "counting");
+    }
     bt::free_csr(P.g, al);
     // k_max: the largest k with at least k edges of support >= k (Section V-C)
     uint64_t kmax = 0;
@@ -828,18 +873,23 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
             Prepared Q;
             rc = prepare(h, cand, hc[0], nU, nL, (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, Q, al);
             bt::Index ix;
-            if (rc == BT_OK) rc = count_and_index(h, Q, sup_c, true, ix, bf, al, cass);
+            if (rc == BT_OK) {
+                cudaError_t es = bt::scatter_u8(cass, Q.g.newid, cass_int, hc[0], al);
+                if (es != cudaSuccess) rc = cuda_fail(h, es, "extracting a candidate subgraph");
+            }
+            if (rc == BT_OK) rc = count_and_index(h, Q, sup_c, true, ix, bf, al, cass_int);
             bt::free_csr(Q.g, al);
             bt::PeelResult pr;
             if (rc == BT_OK) {
                 bt::PeelOpts o;
-                o.assigned = cass;
+                o.assigned = cass_int;
                 o.m_active = hc[1];
                 o.k_init = eps > 0 ? (long long)eps - 1 : 0;
                 o.assign_from = (long long)eps;
                 e = cudaMemsetAsync(phi_local, 0xFF, 4 * hc[0], h->stream);
                 if (e == cudaSuccess) e = bt::peel(ix, sup_c, phi_local, pr, h->num_sms, al, h->peel_seg, &o);
-                if (e == cudaSuccess) e = bt::settle(cmap, hc[0], cass, phi_local, d_phi, d_asg, al);
+                if (e == cudaSuccess) e = bt::gather_u32(phi_local, ix.newid, phi_c, hc[0], al);
+                if (e == cudaSuccess) e = bt::settle(cmap, hc[0], cass, phi_c, d_phi, d_asg, al);
                 if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling a candidate subgraph");
                 else if (pr.status == BT_ERR_OVERFLOW) rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
                 else if (pr.status != BT_OK) rc = fail(h, pr.status, "peeling stopped: device barrier timeout or round limit");
@@ -873,6 +923,8 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
     al.put(sup_c);
     al.put(hist);
     al.put(counts);
+    al.put(cass_int);
+    al.put(phi_c);
     call_end(h, al);
     if (rc == BT_OK) {
         h->last.rounds = st.rounds;

@@ -96,6 +96,11 @@ struct Csr {
     uint32_t *hv = nullptr;   // [n] #neighbours of lower rank (a prefix of the list)
     uint32_t *pl = nullptr;   // [2m] for arc (u->v), v<u: #w in N(v) with w<u; else 0
     uint64_t *wv = nullptr;   // [n] priority-obeyed wedges started at each vertex
+    // Internal edge ids: an edge is numbered by its position in the lower-rank
+    // prefix of its higher-ranked endpoint, so the edges of one vertex are
+    // contiguous (blooms anchored there touch neighbouring words).  eid holds
+    // internal ids; newid maps input id -> internal id.
+    uint32_t *newid = nullptr;  // [m]
 };
 
 // Builds the CSR (and wedge prefix lengths) from a device edge list.
@@ -103,6 +108,11 @@ struct Csr {
 cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
                       Csr &g, uint32_t *err_word, Alloc &al);
 void free_csr(Csr &g, Alloc &al);
+// out[e] = in[newid[e]]: a per-edge array in internal order back to input order.
+cudaError_t gather_u64(const uint64_t *in, const uint32_t *newid, uint64_t *out, uint64_t m, Alloc &al);
+cudaError_t gather_u32(const uint32_t *in, const uint32_t *newid, uint32_t *out, uint64_t m, Alloc &al);
+// out[newid[e]] = in[e]: a per-edge byte array in input order to internal order.
+cudaError_t scatter_u8(const uint8_t *in, const uint32_t *newid, uint8_t *out, uint64_t m, Alloc &al);
 // In-place relabelling of ng concatenated edge lists (graph g owns edges
 // [goff[g], goff[g+1])) into one disjoint union; range errors set kErrRange
 // and the lowest failing graph index in *bad_graph.
@@ -137,6 +147,7 @@ struct Index {
     uint32_t *pair_bloom = nullptr;  // [w2]
     uint64_t *inc_off = nullptr;     // [m+1]
     uint32_t *inc = nullptr;         // [2*w2] pair ids linked to each edge
+    uint32_t *newid = nullptr;       // [m] input edge id -> internal id (ids above are internal)
     size_t bytes() const {
         return nb * 8 + 4 + w2 * 12 + (m + 1) * 8 + w2 * 8;
     }

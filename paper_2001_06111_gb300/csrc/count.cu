@@ -396,6 +396,7 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
 }
 
 void free_index(Index &ix, Alloc &al) {
+    al.put(ix.newid);
     al.put(ix.bloom_k);
     al.put(ix.bloom_off);
     al.put(ix.pairs);

@@ -121,6 +121,39 @@ __global__ void k_wedge_prefix(const uint64_t *off, const uint32_t *adj, uint32_
     }
 }
 
+// Warp per vertex u: its lower-rank prefix edges get internal ids
+// hoff[u] .. hoff[u] + hv[u] - 1.
+__global__ void k_newid(const uint64_t *off, const uint32_t *eid, const uint32_t *hv,
+                        const uint32_t *hoff, uint32_t n, uint32_t *newid) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t u = warp; u < n; u += nwarps) {
+        const uint64_t a = off[u];
+        const uint32_t h = hv[u], base = hoff[u];
+        for (uint32_t i = lane; i < h; i += 32) newid[eid[a + i]] = base + i;
+    }
+}
+
+__global__ void k_relabel(uint32_t *eid, uint64_t na, const uint32_t *newid) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < na;
+         j += (uint64_t)gridDim.x * blockDim.x)
+        eid[j] = newid[eid[j]];
+}
+
+template <typename T>
+__global__ void k_gather(const T *in, const uint32_t *newid, T *out, uint64_t m) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x)
+        out[e] = in[newid[e]];
+}
+
+__global__ void k_scatter_u8(const uint8_t *in, const uint32_t *newid, uint8_t *out, uint64_t m) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < m;
+         e += (uint64_t)gridDim.x * blockDim.x)
+        out[newid[e]] = in[e];
+}
+
 inline unsigned grid_for(uint64_t items, int threads, unsigned cap = 152 * 32) {
     uint64_t g = (items + threads - 1) / threads;
     if (g == 0) g = 1;
@@ -221,6 +254,19 @@ cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t 
     k_wedge_prefix<<<grid_for((uint64_t)n * 32, 256), 256, 0, al.stream>>>(g.off, g.adj, n, g.hv,
                                                                            g.pl, g.wv);
     al.launches++;
+    // internal edge ids grouped by the higher-ranked endpoint
+    {
+        uint32_t *hoff = al.get<uint32_t>(n);
+        g.newid = al.get<uint32_t>(m);
+        if (al.err != cudaSuccess) return al.err;
+        BT_CUDA(exclusive_scan_u32(g.hv, hoff, n, nullptr, al));
+        k_newid<<<grid_for((uint64_t)n * 32, 256), 256, 0, al.stream>>>(g.off, g.eid, g.hv, hoff, n,
+                                                                         g.newid);
+        al.launches++;
+        k_relabel<<<grid_for(na, 256), 256, 0, al.stream>>>(g.eid, na, g.newid);
+        al.launches++;
+        al.put(hoff);
+    }
     al.mark(kPhCsr, true);
     al.put(deg);
     al.put(order);
@@ -229,7 +275,30 @@ cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t 
     return cudaGetLastError();
 }
 
+cudaError_t gather_u64(const uint64_t *in, const uint32_t *newid, uint64_t *out, uint64_t m, Alloc &al) {
+    if (m == 0) return cudaSuccess;
+    k_gather<uint64_t><<<grid_for(m, 256), 256, 0, al.stream>>>(in, newid, out, m);
+    al.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t gather_u32(const uint32_t *in, const uint32_t *newid, uint32_t *out, uint64_t m, Alloc &al) {
+    if (m == 0) return cudaSuccess;
+    k_gather<uint32_t><<<grid_for(m, 256), 256, 0, al.stream>>>(in, newid, out, m);
+    al.launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t scatter_u8(const uint8_t *in, const uint32_t *newid, uint8_t *out, uint64_t m, Alloc &al) {
+    if (m == 0) return cudaSuccess;
+    k_scatter_u8<<<grid_for(m, 256), 256, 0, al.stream>>>(in, newid, out, m);
+    al.launches++;
+    return cudaGetLastError();
+}
+
+// Frees the CSR (and newid unless a caller took it over).
 void free_csr(Csr &g, Alloc &al) {
+    al.put(g.newid);
     al.put(g.off);
     al.put(g.adj);
     al.put(g.eid);

@@ -86,9 +86,11 @@ extern "C" int bt_count_support_static(const int32_t *d_edges, uint64_t m, uint3
     if (hw & bt::kErrRange) return BT_ERR_RANGE;
     if (hw & bt::kErrDup) return BT_ERR_DUP;
     bt::CountOut co;
-    co.support = d_support_out;
+    co.support = al.get<uint64_t>(m);  // internal edge order, gathered below
+    if (!co.support) return BT_ERR_TOO_LARGE;
     e = bt::count_wedges(g, co, kStaticSms < num_sms ? kStaticSms : num_sms, al);
     if (e == cudaErrorMemoryAllocation) return BT_ERR_TOO_LARGE;
+    if (e == cudaSuccess) e = bt::gather_u64(co.support, g.newid, d_support_out, m, al);
     if (e == cudaSuccess) e = cudaStreamSynchronize(al.stream);
     return e == cudaSuccess ? BT_OK : BT_ERR_CUDA;
 }
