@@ -2,12 +2,12 @@
 // Alg. 5, BiT-BU++; the <= k frontier rule of Alg. 4).
 //
 // One round removes the batch S = {unassigned e : support(e) <= k} at once:
-//   incidence phase (Alg. 5, the loop over e in S and B in N_I(e)):
+//   kills (Alg. 5, the loop over e in S and B in N_I(e)):
 //     every live twin pair of a bloom B that holds an edge of S dies once;
-//     C(B) counts the dead pairs.  When both twins are in S the one with the
-//     smaller edge id owns the pair, so a pair is counted once (the example of
-//     Section V-B: three twin pairs of B0 drop its bloom number to 0).  A twin
-//     outside S loses all k_B - 1 butterflies it had in B (Lemma 2).
+//     C(B) counts the dead pairs.  When both twins are in S the pair is
+//     counted once (the example of Section V-B: three twin pairs of B0 drop
+//     its bloom number to 0).  A twin outside S loses all k_B - 1
+//     butterflies it had in B (Lemma 2).
 //   bloom phase (Alg. 5, the loop over blooms with C(B) > 0):
 //     every edge of a surviving pair of B loses C(B) butterflies (one per
 //     dead pair); then k_B -= C(B), so the bloom keeps C(k_B - C, 2)
@@ -20,18 +20,26 @@
 // phi.  An edge joins the next batch exactly when one decrement carries its
 // support from above k to <= k, so rounds inside a level never rescan edges.
 //
-// The whole loop runs in one persistent cooperative kernel (one block per SM
-// slot the occupancy allows).  Phases are separated by a grid barrier whose
-// wait is bounded by a timer; on timeout the kernel raises an error word and
-// every block returns.  Work is split into items of at most kSeg entries: an
-// edge of S with a long link list becomes several incidence items, and a
-// touched bloom with many pairs several bloom items, so no warp straggles on
-// a hub.  A twin pair carries the round it died in; the edges of S race to
-// stamp it with atomicCAS, so exactly one of them counts it in C(B) (the
-// twin rule above, without reading the twin's state), and the twin
-// decrements are applied by the bloom phase, which sees which pairs died in
-// this round.  Counters and work lists are double- or triple-buffered by
-// round, which leaves two barriers per round.  Data written by other blocks
+// Scheduling.  The whole loop runs in one persistent cooperative kernel (one
+// block per SM slot the occupancy allows); phases are separated by a grid
+// barrier whose wait is bounded by a timer (on timeout the kernel raises an
+// error word and every block returns).  The kills of round r + 1 need only
+// C_r, which is final once the bloom phase of round r starts, so they are
+// made inside that bloom phase: the warp whose decrement carries an edge
+// into the batch of round r + 1 kills the edge's twin pairs at once when the
+// edge has few links, and queues the links as incidence items otherwise.  A
+// round therefore costs one barrier, plus a separate incidence phase (and a
+// second barrier) only when such items exist or a level jump selected the
+// batch.  Pairs killed early carry stamp r + 1 and still count as alive in
+// the bloom phase of round r.  The bloom number at the start of round q is
+// the value recorded after the last round that touched the bloom, less
+// C_{q-1} when round q - 1 touched it and its bloom phase has not recorded
+// the new value yet.  Work is split into items of at most kSeg entries, so no
+// warp straggles on a hub edge or bloom.  A twin pair carries the round it
+// died in; the edges of a batch race to stamp it with atomicCAS, so exactly
+// one of them counts it in C(B).  Counters and work lists rotate by round
+// (C by 3, bloom items by 4, batch sizes by 3, incidence items by 2) so each
+// is reset a barrier after its last reader.  Data written by other blocks
 // during the kernel is read with L2 (.cg) loads.
 #include "bt_device.cuh"
 #include "bt_internal.cuh"
@@ -48,18 +56,24 @@ constexpr int kPeelThreads = 1024;
 // multiples of 32 * nwarps): a round with fewer items than warps still gives
 // every item its own warp, and a large round fills all lanes.
 constexpr uint32_t kSmall = 2;
+// edges that join the next batch in a bloom phase are listed per block (up to
+// kJoinCap); the block kills their twin pairs at the end of the phase, two
+// links per thread, for the edges whose links fit in the first kBlockLinks
+constexpr uint32_t kJoinCap = kPeelThreads;
+constexpr uint32_t kBlockLinks = 2 * kPeelThreads;
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
 constexpr uint32_t kErrBarrier = 1u;
 constexpr uint32_t kErrRounds = 2u;
 constexpr uint32_t kErrPeelOverflow = 4u;
+constexpr unsigned kFull = 0xffffffffu;
 
 struct Ctl {
     unsigned long long bar_count;  // barrier arrivals (monotonic within a launch)
     unsigned int err;
     unsigned int pad0;
-    unsigned int n_items[2];  // incidence items per round parity
-    unsigned int n_edges[2];  // frontier edges per round parity
-    unsigned int n_bseg[3];   // bloom items per round mod 3
+    unsigned int n_items[2];  // incidence items, by round parity
+    unsigned int n_edges[3];  // batch sizes, by round mod 3
+    unsigned int n_bseg[4];   // bloom items, by round mod 4
     unsigned int n_alive[2];  // alive list sizes (ping-pong)
     unsigned int n_near[2];   // near-window list sizes (ping-pong)
     unsigned int pad1;
@@ -71,6 +85,7 @@ struct Ctl {
     unsigned long long levels;
     unsigned long long windows;
     unsigned long long kfinal;
+    unsigned long long inc_phases;  // rounds that ran a separate incidence phase
 };
 
 struct PeelArgs {
@@ -83,14 +98,15 @@ struct PeelArgs {
     long long *sup;
     uint32_t *state;
     uint32_t *phi;
-    uint32_t *died;    // round a twin pair died in (kAlive while alive)
-    uint32_t *bk;
-    uint32_t *Cb[3];
-    uint4 *items[2];   // (edge, first link lo, first link hi, count | head flag << 31)
-    uint4 *bseg[3];    // (bloom, first pair, count | head flag << 31, bloom number at round start)
+    uint32_t *died;           // round a twin pair died in (kAlive while alive)
+    unsigned long long *bw;   // per bloom: last round that touched it << 32 | k_B after it
+    uint32_t *Cb[3];          // C_r by round mod 3
+    uint4 *items[2];          // (edge, first link lo, first link hi, count | head flag << 31)
+    uint4 *bseg[4];           // (bloom, first pair, count | head flag << 31, k_B at round start)
     uint32_t *alive[2];
     uint32_t *near[2];
     uint64_t item_cap;
+    uint64_t bseg_cap;
     Ctl *ctl;
     uint64_t round_limit;
     // progressive compression: peel only the m_active unassigned edges, start
@@ -115,7 +131,6 @@ __device__ __forceinline__ unsigned long long now_ns() {
 }
 
 __device__ __forceinline__ uint32_t ldcg_u32(const uint32_t *p) { return __ldcg(p); }
-__device__ __forceinline__ unsigned int ldcg_ui(const unsigned int *p) { return __ldcg(p); }
 __device__ __forceinline__ long long ldcg_ll(const long long *p) { return __ldcg(p); }
 
 // Grid-wide barrier over all blocks of a cooperative launch.  Arrivals go
@@ -131,7 +146,20 @@ __device__ __forceinline__ unsigned long long load_acquire(const unsigned long l
     return v;
 }
 
-__device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no) {
+// Counters the next phase needs.  Thread 0 of each block reads them once
+// after the barrier and hands them to its block through shared memory, so a
+// counter that every thread needs costs one L2 request per block instead of
+// one per warp (same-address requests queue up at one L2 slice).
+struct Snap {
+    const unsigned int *u[5];
+    const unsigned long long *w;
+};
+struct SnapVals {
+    unsigned int u[5];
+    unsigned long long w;
+};
+
+__device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no, const Snap &sn, SnapVals *s_v) {
     __syncthreads();
     __shared__ int s_ok;
     const unsigned long long target = (bar_no + 1) * gridDim.x;
@@ -156,21 +184,29 @@ __device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no) {
                 }
             }
         }
+        if (ok) {
+            unsigned int v[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) v[i] = sn.u[i] ? __ldcg(sn.u[i]) : 0u;
+            const unsigned long long w = sn.w ? __ldcg(sn.w) : 0ull;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) s_v->u[i] = v[i];
+            s_v->w = w;
+        }
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
 }
 
-// Queue edge e (links [ib, ie)) for the round `next_round`: one incidence
-// item per kSeg links, each carrying its link range.
+// Queue the links [ib, ie) of edge e as incidence items of list dst, one item
+// per kSeg links, each carrying its link range.
 template <uint32_t kSeg>
-__device__ __forceinline__ void push_edge(const PeelArgs &a, uint32_t e, uint32_t dst,
-                                          uint32_t next_round, uint64_t ib, uint64_t ie, long long k) {
-    a.state[e] = next_round;
-    if (k >= a.assign_from) a.phi[e] = (uint32_t)k;  // e leaves in a batch of this level
+__device__ __forceinline__ void push_items(const PeelArgs &a, uint32_t e, uint32_t dst, uint64_t ib,
+                                           uint64_t ie) {
     const uint64_t d = ie - ib;
-    const uint32_t nseg = d == 0 ? 1u : (uint32_t)((d + kSeg - 1) / kSeg);
+    if (d == 0) return;
+    const uint32_t nseg = (uint32_t)((d + kSeg - 1) / kSeg);
     const uint32_t base = atomicAdd(&a.ctl->n_items[dst], nseg);
     for (uint32_t s = 0; s < nseg; ++s) {
         const uint64_t j = ib + (uint64_t)s * kSeg;
@@ -179,30 +215,27 @@ __device__ __forceinline__ void push_edge(const PeelArgs &a, uint32_t e, uint32_
         a.items[dst][base + s] =
             make_uint4(e, (uint32_t)j, (uint32_t)(j >> 32), cnt | (s == 0 ? 0x80000000u : 0u));
     }
-    atomicAdd(&a.ctl->n_edges[dst], 1u);
+}
+
+// Edge e joins the batch of round q at level k.
+__device__ __forceinline__ void join_batch(const PeelArgs &a, uint32_t e, uint32_t q, long long k) {
+    a.state[e] = q;
+    if (k >= a.assign_from) a.phi[e] = (uint32_t)k;  // e leaves in a batch of this level
 }
 
 __device__ __forceinline__ void push_near(const PeelArgs &a, uint32_t e, uint32_t nq) {
     a.near[nq][atomicAdd(&a.ctl->n_near[nq], 1u)] = e;
 }
 
-// Subtract dec from support(e).  Queue e for the next round when this takes
-// it from > k to <= k, and list it in the near window when it falls below khi.
-template <uint32_t kSeg>
-__device__ __forceinline__ void decrement(const PeelArgs &a, uint32_t e, long long dec, const Lvl &L,
-                                          uint32_t dst, uint32_t next_round, bool have_range,
-                                          uint64_t ib, uint64_t ie) {
+// Subtract dec from support(e); list e in the near window when it falls
+// below khi.  Returns true when this decrement takes e from > k to <= k, i.e.
+// e joins the next batch (exactly one decrement does).
+__device__ __forceinline__ bool decrement(const PeelArgs &a, uint32_t e, long long dec, const Lvl &L) {
     const long long old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.sup[e]),
                                                (unsigned long long)(-dec));
     const long long now = old - dec;
-    if (old > L.k && now <= L.k) {
-        if (!have_range) {
-            ib = a.inc_off[e];
-            ie = a.inc_off[e + 1];
-        }
-        push_edge<kSeg>(a, e, dst, next_round, ib, ie, L.k);
-    }
     if (old >= L.khi && now < L.khi) push_near(a, e, L.nq);
+    return old > L.k && now <= L.k;
 }
 
 // Window above the current minimum: narrow enough that a level jump scans few
@@ -213,50 +246,70 @@ __device__ __forceinline__ long long window_top(long long kmin) {
     return kmin + (w < 8 ? 8 : w);
 }
 
-// Incidence phase, one killed pair of bloom B: count it in C(B) and, for the
-// first kill of B this round, queue B's pairs as bloom items (each records the
-// bloom number k_B at round start).
+// One kill of a pair of bloom B for round q: count it in C_q(B) and, for the
+// first kill of B in round q, queue B's pairs as bloom items of round q, each
+// recording k_B at the start of round q.
 template <uint32_t kSeg>
-__device__ __forceinline__ void count_kill(const PeelArgs &a, uint32_t *C, uint32_t B, uint32_t c3) {
-    const uint32_t bkB = __ldcg(&a.bk[B]);
+__device__ __forceinline__ void count_kill(const PeelArgs &a, uint32_t B, uint32_t q) {
     const uint32_t bo0 = a.bloom_off[B], bo1 = a.bloom_off[B + 1];
-    if (atomicAdd(&C[B], 1u) == 0u) {
+    const unsigned long long w = __ldcg(&a.bw[B]);
+    const uint32_t cprev = __ldcg(&a.Cb[(q + 2u) % 3u][B]);  // C_{q-1}(B)
+    if (atomicAdd(&a.Cb[q % 3u][B], 1u) == 0u) {
+        const uint32_t kB = (uint32_t)(w >> 32) == q - 1u ? (uint32_t)w : (uint32_t)w - cprev;
         const uint32_t span = bo1 - bo0;
         const uint32_t nseg = (span + kSeg - 1) / kSeg;
-        const uint32_t base = atomicAdd(&a.ctl->n_bseg[c3], nseg);
+        const uint32_t qb = q & 3u;
+        const uint32_t base = atomicAdd(&a.ctl->n_bseg[qb], nseg);
         for (uint32_t s = 0; s < nseg; ++s) {
             const uint32_t left = span - s * kSeg;
-            a.bseg[c3][base + s] =
-                make_uint4(B, bo0 + s * kSeg, (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u), bkB);
+            a.bseg[qb][base + s] =
+                make_uint4(B, bo0 + s * kSeg, (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u), kB);
         }
     }
 }
 
-// Bloom phase, one pair slot (died stamp d, members pr) of a bloom with c
-// pairs killed this round and bloom number kB at round start.
+// Edge e joins the batch of round q in a bloom phase: it goes to the block's
+// list, or, when that is full, the lane queues its links itself.
+template <uint32_t kSeg>
+__device__ __forceinline__ void join_next(const PeelArgs &a, uint32_t e, uint32_t q, long long k,
+                                          uint32_t *s_je, uint32_t *s_jn) {
+    const uint32_t slot = atomicAdd(s_jn, 1u);
+    if (slot < kJoinCap) {
+        s_je[slot] = e;
+    } else {
+        join_batch(a, e, q, k);
+        push_items<kSeg>(a, e, q & 1u, a.inc_off[e], a.inc_off[e + 1]);
+        atomicAdd(&a.ctl->n_edges[q % 3u], 1u);
+    }
+}
+
+// Bloom phase of round r, one pair slot (died stamp d, members pr) of a bloom
+// with c pairs killed this round and bloom number kB at round start.
 template <uint32_t kSeg>
 __device__ __forceinline__ void apply_slot(const PeelArgs &a, uint32_t d, uint2 pr, uint32_t c, uint32_t kB,
-                                           const Lvl &L, uint32_t np, uint32_t round,
-                                           unsigned long long &upd) {
+                                           const Lvl &L, uint32_t round, unsigned long long &upd,
+                                           uint32_t *s_je, uint32_t *s_jn) {
     // bit 31 flags an edge whose bitruss number is already known: it is never
     // peeled again, so it needs no decrement
     const bool fx = pr.x >> 31, fy = pr.y >> 31;
     const uint32_t ex = pr.x & 0x7FFFFFFFu, ey = pr.y & 0x7FFFFFFFu;
-    if (d == kAlive) {
-        // a surviving pair: one butterfly lost per dead pair
-        if (!fx) decrement<kSeg>(a, ex, c, L, np, round + 1, false, 0, 0);
-        if (!fy) decrement<kSeg>(a, ey, c, L, np, round + 1, false, 0, 0);
+    const uint32_t q = round + 1u;
+    if (d == kAlive || d == q) {
+        // alive during this round (a pair killed for the next round still is):
+        // one butterfly lost per dead pair
+        if (!fx && decrement(a, ex, c, L)) join_next<kSeg>(a, ex, q, L.k, s_je, s_jn);
+        if (!fy && decrement(a, ey, c, L)) join_next<kSeg>(a, ey, q, L.k, s_je, s_jn);
         upd += (fx ? 0 : 1) + (fy ? 0 : 1);
     } else if (d == round && kB > 1u) {
         // died now: a member outside S loses its k_B - 1 butterflies
         const uint32_t sx = fx ? round : __ldcg(&a.state[ex]);
         const uint32_t sy = fy ? round : __ldcg(&a.state[ey]);
         if (sx != round) {
-            decrement<kSeg>(a, ex, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+            if (decrement(a, ex, (long long)kB - 1, L)) join_next<kSeg>(a, ex, q, L.k, s_je, s_jn);
             ++upd;
         }
         if (sy != round) {
-            decrement<kSeg>(a, ey, (long long)kB - 1, L, np, round + 1, false, 0, 0);
+            if (decrement(a, ey, (long long)kB - 1, L)) join_next<kSeg>(a, ey, q, L.k, s_je, s_jn);
             ++upd;
         }
     }
@@ -278,10 +331,24 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     bool level_jump = true;
     unsigned long long upd = 0, slots = 0;
     unsigned long long bar_no = 0;  // barriers passed (identical in every block)
+    // edges this block's bloom items carried into the next batch
+    __shared__ uint32_t s_je[kJoinCap], s_joff[kJoinCap], s_jd[kJoinCap];
+    __shared__ unsigned long long s_jib[kJoinCap];
+    __shared__ uint32_t s_jn;
+    __shared__ SnapVals s_v;
+    if (threadIdx.x == 0) s_jn = 0;
+    __syncthreads();
+    // list sizes, kept identically by every thread from the barrier snapshots
+    uint32_t v_near = 0;                      // near list L.nq
+    uint32_t v_alive = (uint32_t)a.m;         // alive list ap
+    uint32_t n_batch = 0, n_items = 0;        // this round's batch and incidence items
+    uint32_t nb_cur = 0, nb_prev = 0;         // bloom items of this round and of the last
 
     while (remaining > 0) {
-        const uint32_t par = round & 1u, np = par ^ 1u;
+        const uint32_t par = round & 1u;
         const uint32_t c3 = round % 3u;
+        const uint32_t b4 = round & 3u;
+        const uint32_t bp = (round + 3u) & 3u;  // previous round's bloom items
         if (round > a.round_limit) {
             if (gtid == 0) atomicOr(&ctl->err, kErrRounds);
             break;
@@ -289,13 +356,12 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
         if (level_jump) {
             // L1: minimum over the near window, compacting it
             {
-                const uint32_t nn = ldcg_ui(&ctl->n_near[L.nq]);
                 unsigned long long best = ~0ull;
-                for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < nn; i0 += nthreads) {
+                for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < v_near; i0 += nthreads) {
                     const uint32_t i = i0 + threadIdx.x;
                     bool keep = false;
                     uint32_t e = 0;
-                    if (i < nn) {
+                    if (i < v_near) {
                         e = ldcg_u32(&a.near[L.nq][i]);
                         if (ldcg_u32(&a.state[e]) == kAlive) {
                             keep = true;
@@ -303,35 +369,38 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                             best = sv < best ? sv : best;
                         }
                     }
-                    const unsigned int mask = __ballot_sync(0xffffffffu, keep);
+                    const unsigned int mask = __ballot_sync(kFull, keep);
                     if (mask) {
                         unsigned int base = 0;
                         if (lane == 0) base = atomicAdd(&ctl->n_near[L.nq ^ 1u], (unsigned)__popc(mask));
-                        base = __shfl_sync(0xffffffffu, base, 0);
+                        base = __shfl_sync(kFull, base, 0);
                         if (keep) a.near[L.nq ^ 1u][base + __popc(mask & ((1u << lane) - 1u))] = e;
                     }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+                    const unsigned long long y = __shfl_xor_sync(kFull, best, o);
                     best = y < best ? y : best;
                 }
                 if (lane == 0 && best != ~0ull) atomicMin(&ctl->minsup, best);
             }
-            if (!grid_barrier(ctl, bar_no)) break;
-            unsigned long long mn = __ldcg(&ctl->minsup);
+            {
+                const Snap sn{{nullptr, nullptr, nullptr, nullptr, &ctl->n_near[L.nq ^ 1u]}, &ctl->minsup};
+                if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+            }
+            unsigned long long mn = s_v.w;
+            v_near = s_v.u[4];
             L.nq ^= 1u;
             if (gtid == 0) ctl->n_near[L.nq ^ 1u] = 0;
             if (mn == ~0ull) {
                 // the window holds no alive edge: rebuild it from all alive edges.
                 // W1: overall minimum, compacting the alive list
-                const uint32_t na = ldcg_ui(&ctl->n_alive[ap]);
                 unsigned long long best = ~0ull;
-                for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < na; i0 += nthreads) {
+                for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < v_alive; i0 += nthreads) {
                     const uint32_t i = i0 + threadIdx.x;
                     bool keep = false;
                     uint32_t e = 0;
-                    if (i < na) {
+                    if (i < v_alive) {
                         e = ldcg_u32(&a.alive[ap][i]);
                         if (ldcg_u32(&a.state[e]) == kAlive) {
                             keep = true;
@@ -339,34 +408,41 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                             best = sv < best ? sv : best;
                         }
                     }
-                    const unsigned int mask = __ballot_sync(0xffffffffu, keep);
+                    const unsigned int mask = __ballot_sync(kFull, keep);
                     if (mask) {
                         unsigned int base = 0;
                         if (lane == 0) base = atomicAdd(&ctl->n_alive[ap ^ 1u], (unsigned)__popc(mask));
-                        base = __shfl_sync(0xffffffffu, base, 0);
+                        base = __shfl_sync(kFull, base, 0);
                         if (keep) a.alive[ap ^ 1u][base + __popc(mask & ((1u << lane) - 1u))] = e;
                     }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+                    const unsigned long long y = __shfl_xor_sync(kFull, best, o);
                     best = y < best ? y : best;
                 }
                 if (lane == 0 && best != ~0ull) atomicMin(&ctl->minsup2, best);
-                if (!grid_barrier(ctl, bar_no)) break;
-                mn = __ldcg(&ctl->minsup2);
+                {
+                    const Snap sn{{nullptr, nullptr, nullptr, nullptr, &ctl->n_alive[ap ^ 1u]}, &ctl->minsup2};
+                    if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+                }
+                mn = s_v.w;
                 if (mn == ~0ull) break;  // no alive edge: cannot happen while remaining > 0
+                v_alive = s_v.u[4];
                 L.khi = window_top((long long)mn);
                 ap ^= 1u;
                 if (gtid == 0) ctl->n_alive[ap ^ 1u] = 0;
                 // W2: list every alive edge below the new window top
-                const uint32_t na2 = ldcg_ui(&ctl->n_alive[ap]);
-                for (uint32_t i = gtid; i < na2; i += nthreads) {
+                for (uint32_t i = gtid; i < v_alive; i += nthreads) {
                     const uint32_t e = ldcg_u32(&a.alive[ap][i]);
                     if (ldcg_ll(&a.sup[e]) < L.khi) push_near(a, e, L.nq);
                 }
                 if (gtid == 0) atomicAdd(&ctl->windows, 1ull);
-                if (!grid_barrier(ctl, bar_no)) break;
+                {
+                    const Snap sn{{nullptr, nullptr, nullptr, nullptr, &ctl->n_near[L.nq]}, nullptr};
+                    if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+                }
+                v_near = s_v.u[4];
                 if (gtid == 0) ctl->minsup2 = ~0ull;
             }
             if ((long long)mn > L.k) L.k = (long long)mn;
@@ -374,25 +450,42 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 if (gtid == 0) atomicOr(&ctl->err, kErrPeelOverflow);
                 break;
             }
-            // L2: the batch is every window edge with support <= k
-            const uint32_t nn2 = ldcg_ui(&ctl->n_near[L.nq]);
-            for (uint32_t i = gtid; i < nn2; i += nthreads) {
+            // L2: the batch is every window edge with support <= k; their
+            // links become incidence items of this round
+            uint32_t sel = 0;
+            for (uint32_t i = gtid; i < v_near; i += nthreads) {
                 const uint32_t e = ldcg_u32(&a.near[L.nq][i]);
-                if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k)
-                    push_edge<kSeg>(a, e, par, round, a.inc_off[e], a.inc_off[e + 1], L.k);
+                if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k) {
+                    join_batch(a, e, round, L.k);
+                    push_items<kSeg>(a, e, par, a.inc_off[e], a.inc_off[e + 1]);
+                    ++sel;
+                }
             }
+            sel = dev::warp_sum(sel);
+            if (lane == 0 && sel) atomicAdd(&ctl->n_edges[c3], sel);
             if (gtid == 0) atomicAdd(&ctl->levels, 1ull);
-            if (!grid_barrier(ctl, bar_no)) break;
+            {
+                const Snap sn{{&ctl->n_edges[c3], &ctl->n_items[par], &ctl->n_bseg[b4], &ctl->n_bseg[bp],
+                               &ctl->n_near[L.nq]},
+                              nullptr};
+                if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+            }
+            n_batch = s_v.u[0];
+            n_items = s_v.u[1];
+            nb_cur = s_v.u[2];
+            nb_prev = s_v.u[3];
+            v_near = s_v.u[4];
             if (gtid == 0) ctl->minsup = ~0ull;
         }
 
-        // ---------------- incidence phase
-        uint32_t *C = a.Cb[c3];
-        // read before the barrier below: block 0 clears it in the bloom phase
-        const uint32_t n_edges = ldcg_ui(&ctl->n_edges[par]);
-        {
-            const uint32_t n_items = ldcg_ui(&ctl->n_items[par]);
-            if (gtid == 0) ctl->n_bseg[(c3 + 1u) % 3u] = 0;
+        if (gtid == 0) {
+            ctl->n_edges[(round + 2u) % 3u] = 0;  // batch of round - 1: read before the last barrier
+            ctl->n_bseg[(round + 2u) & 3u] = 0;   // bloom items of round - 2: C cleared in round - 1
+        }
+
+        // ---------------- incidence phase (only for queued link lists)
+        if (n_items > 0) {
+            if (gtid == 0) atomicAdd(&ctl->inc_phases, 1ull);
             for (uint32_t base = gwarp; base < n_items; base += nwarps * 32u) {
                 const uint32_t i = base + lane * nwarps;
                 const uint4 it = i < n_items ? __ldcg(&a.items[par][i]) : make_uint4(0, 0, 0, 0);
@@ -410,22 +503,22 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r)
                         if (won[r]) B[r] = a.pair_bloom[p[r]];
-                    // the first edge of S to stamp a pair kills it (once)
+                    // the first edge of the batch to stamp a pair kills it (once)
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r)
                         if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r)
-                        if (won[r]) count_kill<kSeg>(a, C, B[r], c3);
+                        if (won[r]) count_kill<kSeg>(a, B[r], round);
                 }
                 // items with many links: the whole warp, one item at a time
-                unsigned big = __ballot_sync(0xffffffffu, cnt > kSmall);
+                unsigned big = __ballot_sync(kFull, cnt > kSmall);
                 while (big) {
                     const int src = __ffs(big) - 1;
                     big &= big - 1u;
-                    const uint32_t bcnt = __shfl_sync(0xffffffffu, cnt, src);
-                    const uint32_t jlo = __shfl_sync(0xffffffffu, it.y, src);
-                    const uint32_t jhi = __shfl_sync(0xffffffffu, it.z, src);
+                    const uint32_t bcnt = __shfl_sync(kFull, cnt, src);
+                    const uint32_t jlo = __shfl_sync(kFull, it.y, src);
+                    const uint32_t jhi = __shfl_sync(kFull, it.z, src);
                     const uint64_t j0 = ((uint64_t)jhi << 32 | jlo) + lane;
                     uint32_t p[R], B[R];
                     bool won[R];
@@ -442,25 +535,28 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                         if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
 #pragma unroll
                     for (uint32_t r = 0; r < R; ++r)
-                        if (won[r]) count_kill<kSeg>(a, C, B[r], c3);
+                        if (won[r]) count_kill<kSeg>(a, B[r], round);
                 }
             }
+            {
+                const Snap sn{{nullptr, nullptr, &ctl->n_bseg[b4], nullptr, nullptr}, nullptr};
+                if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+            }
+            nb_cur = s_v.u[2];
         }
-        if (!grid_barrier(ctl, bar_no)) break;
 
-        // ---------------- bloom phase
-        if (gtid == 0) {
-            ctl->n_items[par] = 0;
-            ctl->n_edges[par] = 0;
-        }
+        // ---------------- bloom phase of this round, kills of the next
+        if (gtid == 0) ctl->n_items[par] = 0;
         {
-            const uint32_t n_bseg = ldcg_ui(&ctl->n_bseg[c3]);
-            for (uint32_t base = gwarp; base < n_bseg; base += nwarps * 32u) {
+            const uint32_t q = round + 1u;
+            const uint32_t *C = a.Cb[c3];
+            for (uint32_t base = gwarp; base < nb_cur; base += nwarps * 32u) {
                 const uint32_t i = base + lane * nwarps;
-                const uint4 it = i < n_bseg ? __ldcg(&a.bseg[c3][i]) : make_uint4(0, 0, 0, 0);
+                const uint4 it = i < nb_cur ? __ldcg(&a.bseg[b4][i]) : make_uint4(0, 0, 0, 0);
                 const uint32_t cnt = it.z & 0x7FFFFFFFu;
                 const uint32_t c = cnt ? __ldcg(&C[it.x]) : 0u;
-                if (cnt && (it.z >> 31)) a.bk[it.x] = it.w - c;
+                if (cnt && (it.z >> 31))
+                    a.bw[it.x] = (unsigned long long)round << 32 | (uint32_t)(it.w - c);
                 slots += cnt;
                 if (cnt <= kSmall) {
                     uint32_t d[kSmall];
@@ -468,45 +564,112 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r) {
                         const bool act = r < cnt;
-                        d[r] = act ? __ldcg(&a.died[it.y + r]) : round + 1u;  // inactive: no case applies
+                        d[r] = act ? __ldcg(&a.died[it.y + r]) : round + 2u;  // inactive: no case applies
                         pr[r] = act ? a.pairs[it.y + r] : make_uint2(0, 0);
                     }
 #pragma unroll
-                    for (uint32_t r = 0; r < kSmall; ++r) apply_slot<kSeg>(a, d[r], pr[r], c, it.w, L, np, round, upd);
+                    for (uint32_t r = 0; r < kSmall; ++r)
+                        apply_slot<kSeg>(a, d[r], pr[r], c, it.w, L, round, upd, s_je, &s_jn);
                 }
-                unsigned big = __ballot_sync(0xffffffffu, cnt > kSmall);
+                unsigned big = __ballot_sync(kFull, cnt > kSmall);
                 while (big) {
                     const int src = __ffs(big) - 1;
                     big &= big - 1u;
-                    const uint32_t bcnt = __shfl_sync(0xffffffffu, cnt, src);
-                    const uint32_t p0 = __shfl_sync(0xffffffffu, it.y, src) + lane;
-                    const uint32_t kB = __shfl_sync(0xffffffffu, it.w, src);
-                    const uint32_t bc = __shfl_sync(0xffffffffu, c, src);
+                    const uint32_t bcnt = __shfl_sync(kFull, cnt, src);
+                    const uint32_t p0 = __shfl_sync(kFull, it.y, src) + lane;
+                    const uint32_t kB = __shfl_sync(kFull, it.w, src);
+                    const uint32_t bc = __shfl_sync(kFull, c, src);
                     uint32_t d[R];
                     uint2 pr[R];
 #pragma unroll
                     for (uint32_t r = 0; r < R; ++r) {
                         const bool act = lane + 32u * r < bcnt;
-                        d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : round + 1u;
+                        d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : round + 2u;
                         pr[r] = act ? a.pairs[p0 + 32u * r] : make_uint2(0, 0);
                     }
 #pragma unroll
-                    for (uint32_t r = 0; r < R; ++r) apply_slot<kSeg>(a, d[r], pr[r], bc, kB, L, np, round, upd);
+                    for (uint32_t r = 0; r < R; ++r)
+                        apply_slot<kSeg>(a, d[r], pr[r], bc, kB, L, round, upd, s_je, &s_jn);
                 }
             }
             // clear C of the blooms the previous round touched (threads from
             // the top of the grid, away from the bloom items above)
-            const uint32_t cp = (c3 + 2u) % 3u;
-            const uint32_t nprev = ldcg_ui(&ctl->n_bseg[cp]);
-            for (uint32_t i = nthreads - 1u - gtid; i < nprev; i += nthreads) {
-                const uint4 it = __ldcg(&a.bseg[cp][i]);
-                if (it.w) a.Cb[cp][it.x] = 0;
+            uint32_t *Cp = a.Cb[(round + 2u) % 3u];
+            for (uint32_t i = nthreads - 1u - gtid; i < nb_prev; i += nthreads) {
+                const uint4 it = __ldcg(&a.bseg[bp][i]);
+                if (it.z >> 31) Cp[it.x] = 0;
+            }
+
+            // the block kills the twin pairs of the edges it listed
+            __syncthreads();
+            const uint32_t njr = s_jn;
+            const uint32_t nj = njr < kJoinCap ? njr : kJoinCap;
+            if (nj > 0) {
+                uint32_t e = 0, d = 0;
+                uint64_t ib = 0;
+                if (threadIdx.x < nj) {
+                    e = s_je[threadIdx.x];
+                    join_batch(a, e, q, L.k);
+                    ib = a.inc_off[e];
+                    const uint64_t dl = a.inc_off[e + 1] - ib;
+                    d = dl > kBlockLinks ? kBlockLinks + 1u : (uint32_t)dl;  // longer lists are queued
+                }
+                uint32_t total = 0;
+                const uint32_t off = dev::block_excl_scan<uint32_t>(d, &total);
+                if (threadIdx.x < nj) {
+                    s_joff[threadIdx.x] = off;
+                    s_jd[threadIdx.x] = d;
+                    s_jib[threadIdx.x] = ib;
+                    if (off + d > kBlockLinks) push_items<kSeg>(a, e, q & 1u, ib, a.inc_off[e + 1]);
+                }
+                if (threadIdx.x == 0) atomicAdd(&ctl->n_edges[q % 3u], nj);
+                __syncthreads();
+                const uint32_t lim = total < kBlockLinks ? total : kBlockLinks;
+                uint32_t p[2], B[2];
+                bool won[2];
+#pragma unroll
+                for (uint32_t r = 0; r < 2; ++r) {
+                    const uint32_t x = threadIdx.x + r * (uint32_t)kPeelThreads;
+                    won[r] = false;
+                    p[r] = 0;
+                    if (x < lim) {
+                        const uint32_t j = dev::last_le_u32(s_joff, nj, x);
+                        if (s_joff[j] + s_jd[j] <= kBlockLinks) {
+                            won[r] = true;
+                            p[r] = a.inc[s_jib[j] + (x - s_joff[j])];
+                        }
+                    }
+                }
+#pragma unroll
+                for (uint32_t r = 0; r < 2; ++r)
+                    if (won[r]) B[r] = a.pair_bloom[p[r]];
+                // the first edge of the batch to stamp a pair kills it (once)
+#pragma unroll
+                for (uint32_t r = 0; r < 2; ++r)
+                    if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, q) == kAlive;
+#pragma unroll
+                for (uint32_t r = 0; r < 2; ++r)
+                    if (won[r]) count_kill<kSeg>(a, B[r], q);
+                if (threadIdx.x == 0) s_jn = 0;
             }
         }
-        if (!grid_barrier(ctl, bar_no)) break;
-        remaining -= n_edges;
+        {
+            // next round: its batch, incidence items, bloom items, this
+            // round's bloom items (C to clear) and the near list size
+            const uint32_t q = round + 1u;
+            const Snap sn{{&ctl->n_edges[q % 3u], &ctl->n_items[q & 1u], &ctl->n_bseg[q & 3u], &ctl->n_bseg[b4],
+                           &ctl->n_near[L.nq]},
+                          nullptr};
+            if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+        }
+        remaining -= n_batch;
         ++round;
-        level_jump = remaining > 0 && ldcg_ui(&ctl->n_items[np]) == 0;
+        n_batch = s_v.u[0];
+        n_items = s_v.u[1];
+        nb_cur = s_v.u[2];
+        nb_prev = s_v.u[3];
+        v_near = s_v.u[4];
+        level_jump = remaining > 0 && n_batch == 0;
     }
     upd = dev::warp_sum(upd);
     if (lane == 0 && upd) atomicAdd(&ctl->updates, upd);
@@ -522,14 +685,20 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 // never queued.
 constexpr uint32_t kPerm = 0xFFFFFFFEu;
 __global__ void k_peel_init(const uint64_t *support, uint64_t m, long long *sup, uint32_t *state,
-                            const uint8_t *assigned,
-                            uint32_t *alive) {
+                            const uint8_t *assigned, uint32_t *alive) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
          i += (uint64_t)gridDim.x * blockDim.x) {
         sup[i] = (long long)support[i];
         state[i] = (assigned && assigned[i]) ? kPerm : kAlive;
         alive[i] = (uint32_t)i;
     }
+}
+
+// Bloom words: no round has touched the bloom yet, k_B from the index.
+__global__ void k_bw_init(const uint32_t *bloom_k, uint64_t nb, unsigned long long *bw) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nb;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        bw[i] = 0xFFFFFFFFull << 32 | bloom_k[i];
 }
 
 inline unsigned grid_for(uint64_t items, int threads, unsigned cap) {
@@ -546,6 +715,7 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     const uint64_t m = ix.m;
     res = PeelResult{};
     if (m == 0 || (opts && opts->assigned && opts->m_active == 0)) return cudaSuccess;
+    // one round queues each edge and each bloom at most once
     const uint64_t item_cap = m + (2 * ix.w2) / kSeg + 2;
     const uint64_t bseg_cap = ix.nb + ix.w2 / kSeg + 2;
     PeelArgs a{};
@@ -559,17 +729,16 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     a.sup = al.get<long long>(m);
     a.state = al.get<uint32_t>(m);
     a.died = al.get<uint32_t>(ix.w2);
-    a.bk = al.get<uint32_t>(ix.nb);
-    for (int i = 0; i < 3; ++i) {
-        a.Cb[i] = al.get<uint32_t>(ix.nb);
-        a.bseg[i] = al.get<uint4>(bseg_cap);
-    }
+    a.bw = al.get<unsigned long long>(ix.nb);
+    for (int i = 0; i < 3; ++i) a.Cb[i] = al.get<uint32_t>(ix.nb);
+    for (int i = 0; i < 4; ++i) a.bseg[i] = al.get<uint4>(bseg_cap);
     for (int i = 0; i < 2; ++i) {
         a.items[i] = al.get<uint4>(item_cap);
         a.alive[i] = al.get<uint32_t>(m);
         a.near[i] = al.get<uint32_t>(m);
     }
     a.item_cap = item_cap;
+    a.bseg_cap = bseg_cap;
     a.ctl = al.get<Ctl>(1);
     a.round_limit = m + 1;
     a.m_active = (opts && opts->assigned) ? opts->m_active : m;
@@ -583,7 +752,8 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     al.launches++;
     BT_CUDA(cudaMemsetAsync(a.died, 0xFF, sizeof(uint32_t) * (ix.w2 ? ix.w2 : 1), st));
     if (ix.nb) {
-        BT_CUDA(cudaMemcpyAsync(a.bk, ix.bloom_k, sizeof(uint32_t) * ix.nb, cudaMemcpyDeviceToDevice, st));
+        k_bw_init<<<grid_for(ix.nb, 256, (unsigned)num_sms * 16), 256, 0, st>>>(ix.bloom_k, ix.nb, a.bw);
+        al.launches++;
         for (int i = 0; i < 3; ++i)
             BT_CUDA(cudaMemsetAsync(a.Cb[i], 0, sizeof(uint32_t) * ix.nb, st));
     }
@@ -612,14 +782,13 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     res.updates = h.updates;
     res.slots = h.slots;
     res.kmax = h.kfinal;
+    res.inc_phases = h.inc_phases;
     al.put(a.sup);
     al.put(a.state);
     al.put(a.died);
-    al.put(a.bk);
-    for (int i = 0; i < 3; ++i) {
-        al.put(a.Cb[i]);
-        al.put(a.bseg[i]);
-    }
+    al.put(a.bw);
+    for (int i = 0; i < 3; ++i) al.put(a.Cb[i]);
+    for (int i = 0; i < 4; ++i) al.put(a.bseg[i]);
     for (int i = 0; i < 2; ++i) {
         al.put(a.items[i]);
         al.put(a.alive[i]);
