@@ -47,7 +47,7 @@
 namespace bt {
 namespace {
 
-constexpr int kPeelThreads = 1024;
+constexpr int kPeelThreads = 768;  // 80 registers a thread, no spills
 // entries per work item: SEG = 32 or 64 (template parameter picked by the
 // batch autotuner); each lane handles SEG / 32 entries with their loads and
 // atomics issued together.
