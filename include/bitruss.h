@@ -286,6 +286,39 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
                              double tau, uint64_t *support_out, uint32_t *phi_out, bt_pc_stats *stats,
                              uint32_t flags);
 
+/* ---------------------------------------------------------------- hierarchy
+ * The k-bitruss H_k (Def. 4, Section II) is the maximal subgraph in which every
+ * edge lies in at least k butterflies of that subgraph; the bitruss number
+ * phi(e) is the largest k with e in H_k (Def. 5).  The k-bitrusses are nested,
+ * so H_k = {e : phi(e) >= k}: given the phi of bt_decompose (same edge order),
+ * these calls return the hierarchy that the applications of Section I
+ * consume (nested groups, communities at several levels).
+ */
+
+/*
+ * Order the edges by bitruss number, largest first, edges of equal phi in
+ * ascending input index.  Every k-bitruss is then a prefix: H_k is
+ * order_out[0 .. n_k), n_k = number of edges with phi >= k.
+ *   phi            -- u32[m] bitruss numbers, indexed like the input edges
+ *   order_out      -- u32[m] edge indices (caller-allocated)
+ *   phi_sorted_out -- u32[m] or NULL: phi of order_out[i] (non-increasing),
+ *                     for finding n_k by binary search
+ * flags: BT_DEVICE_PTRS only (phi, order_out and phi_sorted_out are then
+ * device pointers).  m must be below 2^32.  Errors: BT_ERR_ARG (NULL pointer,
+ * unknown flag, m too large), BT_ERR_NOMEM, BT_ERR_CUDA.
+ */
+int bt_hierarchy(bt_handle *h, const uint32_t *phi, uint64_t m, uint32_t *order_out,
+                 uint32_t *phi_sorted_out, uint32_t flags);
+
+/*
+ * The edges of one k-bitruss H_k: the indices of the edges with phi >= k, in
+ * ascending order, written to edges_out[0 .. *count_out) (edges_out has room
+ * for m entries; count_out is always a host pointer).  H_0 is every edge.
+ * flags, limits and errors as bt_hierarchy.
+ */
+int bt_k_bitruss(bt_handle *h, const uint32_t *phi, uint64_t m, uint32_t k, uint32_t *edges_out,
+                 uint64_t *count_out, uint32_t flags);
+
 /* ---------------------------------------------------------------- serving
  * A request loop with continuous batching.  Each submitted request is one
  * graph (host pointers, as in bt_graph; the caller keeps edges and outputs

@@ -15,6 +15,11 @@ read-only support count, single-threaded peeling):
 * ``local_check``      -- per selected edge, the count of butterflies whose
   other edges all have phi >= phi(e), and the local h-value (the fixpoint
   property every correct phi satisfies; follows from Defs. 4-5).
+* ``k_bitruss``        -- the k-bitruss H_k straight from Def. 4: delete every
+  edge with fewer than k butterflies in the remaining graph until none is
+  left (Python loop over ``support``).
+* ``hierarchy``        -- edges ordered by bitruss number, largest first, ties
+  in input order (numpy stable sort), so each H_k is a prefix.
 """
 from __future__ import annotations
 
@@ -115,3 +120,30 @@ def local_check(edges, nU: int, nL: int, phi, which):
     _check(_load().oracle_local_check(e.ctypes.data, e.shape[0], nU, nL, p.ctypes.data,
                                       w.ctypes.data, w.shape[0], cnt.ctypes.data, h.ctypes.data))
     return cnt, h
+
+
+def k_bitruss(edges, nU: int, nL: int, k: int) -> np.ndarray:
+    """Bool mask of the edges of the k-bitruss H_k (Def. 4, Section II): the
+    maximal subgraph in which every edge lies in >= k of its butterflies.
+    Deleting all edges below k and recounting until nothing changes reaches it
+    (a deleted edge is in no subgraph with the property, as deletions only
+    lower supports)."""
+    e = _edges(edges)
+    keep = np.ones(e.shape[0], dtype=bool)
+    while True:
+        idx = np.flatnonzero(keep)
+        if idx.size == 0:
+            return keep
+        s = support(e[idx], nU, nL)
+        low = s < np.uint64(k)
+        if not low.any():
+            return keep
+        keep[idx[low]] = False
+
+
+def hierarchy(phi) -> np.ndarray:
+    """Edge ids by bitruss number, largest first, equal phi in ascending id.
+    With H_k = {e : phi_e >= k} (Defs. 4-5; the k-bitrusses are nested) every
+    H_k is the prefix of length |{e : phi_e >= k}|."""
+    p = np.asarray(phi).astype(np.int64)
+    return np.argsort(-p, kind="stable").astype(np.uint32)

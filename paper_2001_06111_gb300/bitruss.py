@@ -34,7 +34,7 @@ EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_
             "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
             "bt_profile_read", "bt_count_support_static", "bt_decompose_batch",
             "bt_server_create", "bt_server_destroy", "bt_server_submit", "bt_server_poll",
-            "bt_server_stats_read", "bt_decompose_progressive")
+            "bt_server_stats_read", "bt_decompose_progressive", "bt_hierarchy", "bt_k_bitruss")
 
 
 class BitrussError(RuntimeError):
@@ -154,6 +154,8 @@ def load(path: str = LIB_PATH):
         lib.bt_index_export.argtypes = [P, P, P, P]
         lib.bt_decompose.argtypes = [P, P, U64, U32, U32, P, P, ctypes.POINTER(PeelStats), U32]
         lib.bt_count_support_static.argtypes = [P, U64, U32, U32, P, U32, P]
+        lib.bt_hierarchy.argtypes = [P, P, U64, P, P, U32]
+        lib.bt_k_bitruss.argtypes = [P, P, U64, U32, P, ctypes.POINTER(U64), U32]
         lib.bt_decompose_batch.argtypes = [P, ctypes.POINTER(Graph), U32, ctypes.POINTER(Tune),
                                            ctypes.POINTER(BatchStats), U32]
         lib.bt_server_create.argtypes = [ctypes.POINTER(P), I, ctypes.POINTER(ServerConfig)]
@@ -252,6 +254,39 @@ def bt_count_support(h: Handle, edges, nU: int, nL: int, support_out=None, flags
     sup, sptr = _out(import_dev, m, np.uint64, _torch_dtype("uint64"), support_out)
     _check(h, load().bt_count_support(h.ptr, ptr, m, nU, nL, sptr, flags | f))
     return sup
+
+
+def _phi_arg(phi):
+    """(pointer, m, flags, keepalive) for a u32 phi array: numpy (host) or CUDA torch tensor (device)."""
+    if _is_torch(phi):
+        import torch
+        assert phi.dtype == _torch_dtype("uint32") and phi.is_contiguous() and phi.dim() == 1
+        return (phi.data_ptr() if phi.numel() else None), phi.numel(), (BT_DEVICE_PTRS if phi.is_cuda else 0), phi
+    a = np.ascontiguousarray(phi, dtype=np.uint32)
+    return (a.ctypes.data if a.size else None), a.size, 0, a
+
+
+def bt_hierarchy(h: Handle, phi, want_phi: bool = True):
+    """Edges by bitruss number, largest first (ties in input order): every
+    k-bitruss H_k is a prefix.  Returns (order u32[m], phi_sorted u32[m] or None)."""
+    ptr, m, f, keep = _phi_arg(phi)
+    dev = keep if f & BT_DEVICE_PTRS else None
+    order, optr = _out(dev, m, np.uint32, _torch_dtype("uint32"), None)
+    ps, pptr = (None, None)
+    if want_phi:
+        ps, pptr = _out(dev, m, np.uint32, _torch_dtype("uint32"), None)
+    _check(h, load().bt_hierarchy(h.ptr, ptr, m, optr, pptr, f))
+    return order, ps
+
+
+def bt_k_bitruss(h: Handle, phi, k: int):
+    """Indices (ascending) of the edges of the k-bitruss H_k, i.e. phi >= k."""
+    ptr, m, f, keep = _phi_arg(phi)
+    dev = keep if f & BT_DEVICE_PTRS else None
+    out, optr = _out(dev, m, np.uint32, _torch_dtype("uint32"), None)
+    n = ctypes.c_uint64(0)
+    _check(h, load().bt_k_bitruss(h.ptr, ptr, m, k, optr, ctypes.byref(n), f))
+    return out[: n.value]
 
 
 def bt_build_index(h: Handle, edges, nU: int, nL: int, flags: int = 0) -> dict:

@@ -307,6 +307,108 @@ int bt_count_support(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU
     return rc;
 }
 
+// Stages a u32[m] array on the device (or uses it in place with BT_DEVICE_PTRS).
+static int stage_u32(bt_handle *h, const uint32_t *src, uint64_t m, uint32_t flags, bt::Alloc &al,
+                     const uint32_t **d_out, uint32_t **owned) {
+    *owned = nullptr;
+    if (flags & BT_DEVICE_PTRS) {
+        *d_out = src;
+        return BT_OK;
+    }
+    *owned = al.get<uint32_t>(m);
+    if (!*owned) return cuda_fail(h, al.err, "staging phi");
+    cudaError_t e = cudaMemcpyAsync(*owned, src, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying phi to the device");
+    *d_out = *owned;
+    return BT_OK;
+}
+
+static int check_phi_args(bt_handle *h, const uint32_t *phi, uint64_t m, const void *out, uint32_t flags) {
+    if (!h) return BT_ERR_ARG;
+    if (flags & ~(uint32_t)BT_DEVICE_PTRS) return fail(h, BT_ERR_ARG, "unknown flag bits 0x%x", flags);
+    if (m >= (1ull << 32)) return fail(h, BT_ERR_ARG, "m = %llu exceeds 2^32 - 1", (unsigned long long)m);
+    if (m > 0 && (!phi || !out)) return fail(h, BT_ERR_ARG, "phi or the output is NULL");
+    return BT_OK;
+}
+
+extern "C" int bt_hierarchy(bt_handle *h, const uint32_t *phi, uint64_t m, uint32_t *order_out,
+                            uint32_t *phi_sorted_out, uint32_t flags) {
+    int rc = check_phi_args(h, phi, m, order_out, flags);
+    if (rc) return rc;
+    h->err.clear();
+    if (m == 0) return BT_OK;
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    const bool dev = flags & BT_DEVICE_PTRS;
+    const uint32_t *d_phi = nullptr;
+    uint32_t *owned = nullptr;
+    rc = stage_u32(h, phi, m, flags, al, &d_phi, &owned);
+    uint32_t *d_order = nullptr, *d_ps = nullptr;
+    if (rc == BT_OK) {
+        d_order = dev ? order_out : al.get<uint32_t>(m);
+        if (phi_sorted_out) d_ps = dev ? phi_sorted_out : al.get<uint32_t>(m);
+        if (al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating the order");
+    }
+    if (rc == BT_OK) {
+        cudaError_t e = bt::hierarchy_order(d_phi, m, d_order, d_ps, al);
+        if (e == cudaSuccess) e = deliver(h, order_out, d_order, sizeof(uint32_t) * m, flags);
+        if (e == cudaSuccess && phi_sorted_out)
+            e = deliver(h, phi_sorted_out, d_ps, sizeof(uint32_t) * m, flags);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "ordering the edges by phi");
+    }
+    if (!dev) {
+        al.put(d_order);
+        al.put(d_ps);
+    }
+    al.put(owned);
+    h->last = bt_profile{};
+    h->last.n_edges = m;
+    h->last.launches = al.launches;
+    cudaStreamSynchronize(h->stream);
+    return rc;
+}
+
+extern "C" int bt_k_bitruss(bt_handle *h, const uint32_t *phi, uint64_t m, uint32_t k, uint32_t *edges_out,
+                            uint64_t *count_out, uint32_t flags) {
+    int rc = check_phi_args(h, phi, m, edges_out, flags);
+    if (rc) return rc;
+    if (!count_out) return fail(h, BT_ERR_ARG, "count_out is NULL");
+    h->err.clear();
+    *count_out = 0;
+    if (m == 0) return BT_OK;
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    const bool dev = flags & BT_DEVICE_PTRS;
+    const uint32_t *d_phi = nullptr;
+    uint32_t *owned = nullptr;
+    rc = stage_u32(h, phi, m, flags, al, &d_phi, &owned);
+    uint32_t *d_out = nullptr;
+    if (rc == BT_OK) {
+        d_out = dev ? edges_out : al.get<uint32_t>(m);
+        if (al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating the edge list");
+    }
+    if (rc == BT_OK) {
+        uint32_t n = 0;
+        cudaError_t e = bt::select_ge(d_phi, m, k, d_out, h->err_word, al);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&n, h->err_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e == cudaSuccess && !dev && n)
+            e = cudaMemcpyAsync(edges_out, d_out, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "selecting the k-bitruss");
+        else *count_out = n;
+    }
+    if (!dev) al.put(d_out);
+    al.put(owned);
+    h->last = bt_profile{};
+    h->last.n_edges = m;
+    h->last.launches = al.launches;
+    cudaStreamSynchronize(h->stream);
+    return rc;
+}
+
 static int build_index_impl(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU,
                             uint32_t nL, uint32_t flags, uint64_t *d_sup, bt::Alloc &al) {
     Prepared P;

@@ -176,6 +176,14 @@ struct PeelOpts {
 cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
                  int num_sms, Alloc &al, int seg = 32, const PeelOpts *opts = nullptr);
 
+// ---------------------------------------------------------------- hierarchy
+// order[i]: edge ids by phi descending, equal phi in ascending id (stable);
+// phi_sorted (nullable) receives phi[order[i]].  m < 2^32.
+cudaError_t hierarchy_order(const uint32_t *phi, uint64_t m, uint32_t *order, uint32_t *phi_sorted, Alloc &al);
+// out[0 .. *d_count): ids of the edges with phi >= k, ascending (d_count: device).
+cudaError_t select_ge(const uint32_t *phi, uint64_t m, uint32_t k, uint32_t *out, uint32_t *d_count,
+                      Alloc &al);
+
 // ---------------------------------------------------------------- progressive compression
 // hist[min(sup, m)] counts over all edges (m + 1 bins, zeroed here).
 cudaError_t support_hist(const uint64_t *sup, uint64_t m, uint32_t *hist, Alloc &al);

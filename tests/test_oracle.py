@@ -153,3 +153,57 @@ def test_local_check_detects_planted_mistakes():
             bad[e] = bad[e] + delta if delta > 0 else bad[e] - 1
             cnt, h = oracle.local_check(g.edges, g.nU, g.nL, bad, np.array([e]))
             assert not (h[0] == bad[e] and cnt[0] >= bad[e])
+
+
+# ---------------------------------------------------------------- hierarchy
+def test_paper_example_k_bitrusses():
+    # Section I and Example 1 (Section II): H_2 is the six blue edges
+    # e0..e5, H_1 adds the three yellow edges e6..e8, the gray e9, e10 lie only
+    # in H_0 = G.
+    nU, nL, rows = pins.read_golden(os.path.join(GOLDEN, "paper_example_g.txt"))
+    edges = np.array([(int(r[1]), int(r[2])) for r in rows], dtype=np.int32)
+    assert np.flatnonzero(oracle.k_bitruss(edges, nU, nL, 0)).tolist() == list(range(11))
+    assert np.flatnonzero(oracle.k_bitruss(edges, nU, nL, 1)).tolist() == list(range(9))
+    assert np.flatnonzero(oracle.k_bitruss(edges, nU, nL, 2)).tolist() == list(range(6))
+    assert not oracle.k_bitruss(edges, nU, nL, 3).any()
+    # e0..e5 all have phi 2, e6..e8 phi 1: in ascending input order per level
+    assert oracle.hierarchy([2, 2, 2, 2, 2, 2, 1, 1, 1, 0, 0]).tolist() == list(range(11))
+
+
+@pytest.mark.parametrize("a,b", [(2, 2), (3, 4), (5, 3)])
+def test_k_bitruss_of_biclique(a, b):
+    # every edge of K_{a,b} is in (a-1)(b-1) butterflies (Lemmas 1-2)
+    e = pins.biclique(a, b)
+    t = (a - 1) * (b - 1)
+    for k in (0, 1, t, t + 1):
+        assert oracle.k_bitruss(e, a, b, k).all() == (k <= t)
+        assert oracle.k_bitruss(e, a, b, k).any() == (k <= t)
+
+
+def test_k_bitruss_of_disjoint_bicliques():
+    # K_{2,3} (2 butterflies an edge) beside K_{3,3} (4 an edge): H_3 and H_4
+    # are the K_{3,3} alone
+    e = np.concatenate([pins.biclique(2, 3, 0, 0), pins.biclique(3, 3, 2, 3)])
+    for k, want in ((2, np.ones(15, bool)), (3, np.r_[np.zeros(6, bool), np.ones(9, bool)]),
+                    (4, np.r_[np.zeros(6, bool), np.ones(9, bool)]), (5, np.zeros(15, bool))):
+        assert oracle.k_bitruss(e, 5, 6, k).tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_k_bitruss_matches_phi(seed):
+    # Def. 5: phi_e is the largest k whose k-bitruss holds e, so H_k computed by
+    # deletion (Def. 4) and the edges with phi >= k from Alg. 1 peeling agree
+    g = synth.random_tiny(50 + seed, 14, 12, 80)
+    _, phi = oracle.bitruss(g.edges, 14, 12)
+    for k in range(int(phi.max()) + 2):
+        assert oracle.k_bitruss(g.edges, 14, 12, k).tolist() == (phi >= k).tolist()
+
+
+def test_hierarchy_order_by_brute_force():
+    rng = np.random.default_rng(7)
+    phi = rng.integers(0, 6, size=300)
+    order = oracle.hierarchy(phi)
+    assert order.tolist() == sorted(range(300), key=lambda e: (-int(phi[e]), e))
+    for k in range(8):
+        n = int((phi >= k).sum())
+        assert sorted(order[:n].tolist()) == np.flatnonzero(phi >= k).tolist()
