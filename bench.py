@@ -37,6 +37,9 @@ WORKLOADS = {
     "batch": dict(name="batch-4096-chunglu-logU(100,200000)", graphs=4096),
     "serve": dict(name="poisson-serve-batchdist+5%-2M", pool=256, big=4,
                   rates=[50, 100, 200, 500, 1000, 2000], seconds=4.0),
+    # support updates and index sizes, BiT-BU++ against BiT-PC (Figs. 10-11)
+    "updates": dict(name="updates-and-index-size", configs={"small": (0.02, 0.1), "medium": (0.02, 0.1),
+                                                           "large": (0.05,)}),
 }
 WORKLOAD = WORKLOADS["medium"]
 METRIC = "edges decomposed/s"
@@ -285,6 +288,52 @@ def run_batch(args):
     return 0 if exact else 1
 
 
+def run_updates(args):
+    """Per configuration: support updates and BE-Index size of the batch peel
+    (BiT-BU++, one full index) against progressive compression (BiT-PC, one
+    compressed index per pass, the largest reported), with wall times; the
+    bitruss numbers of the two must agree exactly."""
+    from paper_2001_06111_gb300 import bitruss as bt
+    from paper_2001_06111_gb300 import build, synth
+
+    build.build()
+    h = bt.bt_create(0)
+    rows = []
+    exact = True
+    for cfg, taus in WORKLOAD["configs"].items():
+        g = getattr(synth, cfg)()
+        bt.bt_decompose(h, g.edges[: min(g.m, 20000)], g.nU, g.nL)  # warm-up (module, pool)
+        ist = bt.bt_build_index(h, g.edges, g.nU, g.nL)
+        t0 = time.perf_counter()
+        _, phi, st = bt.bt_decompose(h, g.edges, g.nU, g.nL)
+        t_bu = time.perf_counter() - t0
+        row = {"workload": cfg, "m": g.m,
+               "bu": {"support_updates": st["support_updates"], "index_bytes": ist["index_bytes"],
+                      "links": 2 * ist["n_bloom_wedges"], "rounds": st["rounds"], "s": t_bu},
+               "pc": []}
+        for tau in taus:
+            t0 = time.perf_counter()
+            _, phi_pc, pst = bt.bt_decompose_progressive(h, g.edges, g.nU, g.nL, tau=tau)
+            t_pc = time.perf_counter() - t0
+            same = bool(np.array_equal(phi, phi_pc))
+            exact = exact and same
+            row["pc"].append({"tau": tau, "support_updates": pst["support_updates"],
+                              "index_bytes_max": pst["index_bytes_max"], "links": pst["links"],
+                              "passes": pst["passes"], "rounds": pst["rounds"], "s": t_pc,
+                              "phi_equal": same})
+        rows.append(row)
+        print(json.dumps({"partial": row}), file=sys.stderr, flush=True)
+    med = next(r for r in rows if r["workload"] == "medium")
+    line = {"metric": "support updates, BiT-PC / BiT-BU++", "unit": "ratio",
+            "value": med["pc"][0]["support_updates"] / max(1, med["bu"]["support_updates"]),
+            "higher_is_better": False, "n_gpus": 1, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "value_on": "medium, first tau"},
+            "vs_baseline": None, "phi_equal": exact, "configs": rows}
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0 if exact else 1
+
+
 def serve_trace(srv, pool, big, rate, seconds, seed):
     """Submit a Poisson stream (rate req/s for `seconds`) to `srv`: each
     request is a big graph with probability 0.05, else a pool graph.  Returns
@@ -382,6 +431,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "updates":
+        return run_updates(args)
 
     ws, rank, local = dist_env()
     # the CPU baseline runs before the first CUDA call (rank 0, N=1 only)

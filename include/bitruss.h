@@ -265,6 +265,8 @@ typedef struct {
     uint64_t wedges;           /* priority-obeyed wedges of the candidate subgraphs, summed */
     uint64_t k_max;            /* largest k with >= k edges of support >= k */
     uint64_t alpha;            /* eps step, ceil(k_max * tau) */
+    uint64_t index_bytes_max;  /* largest compressed BE-Index of a pass (bytes, as bt_index_stats) */
+    uint64_t links;            /* edge-bloom links stored, summed over passes (assigned edges get none) */
 } bt_pc_stats;
 
 /*

@@ -95,7 +95,8 @@ class PcStats(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
                 ("levels", ctypes.c_uint64), ("support_updates", ctypes.c_uint64),
                 ("candidate_edges", ctypes.c_uint64), ("wedges", ctypes.c_uint64),
-                ("k_max", ctypes.c_uint64), ("alpha", ctypes.c_uint64)]
+                ("k_max", ctypes.c_uint64), ("alpha", ctypes.c_uint64),
+                ("index_bytes_max", ctypes.c_uint64), ("links", ctypes.c_uint64)]
 
 
 class ServerConfig(ctypes.Structure):

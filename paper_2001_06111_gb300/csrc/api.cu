@@ -28,6 +28,7 @@ struct bt_handle {
     bt_profile last{};
     int count_nt = 512;   // schedule used by the next pipeline run
     int peel_seg = 32;
+    int peel_sms = 0;     // SMs the peel kernel spans (0: all); a server worker takes its share
     std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (count_nt, peel_seg)
     unsigned char *pinned = nullptr;  // page-locked staging for batch copies
     size_t pinned_bytes = 0;
@@ -64,6 +65,8 @@ int cuda_fail(bt_handle *h, cudaError_t e, const char *where) {
         return fail(h, BT_ERR_NOMEM, "%s: device allocation failed (%s)", where, cudaGetErrorString(e));
     return fail(h, BT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
+
+int peel_sms(const bt_handle *h) { return h->peel_sms > 0 ? h->peel_sms : h->num_sms; }
 
 bt::Alloc make_alloc(bt_handle *h) {
     bt::Alloc al;
@@ -528,7 +531,7 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
     rc = build_index_impl(h, edges, m, nU, nL, flags, s_int, al);
     bt::PeelResult pr;
     if (rc == BT_OK) {
-        cudaError_t e = bt::peel(h->index, s_int, p_int, pr, h->num_sms, al, h->peel_seg);
+        cudaError_t e = bt::peel(h->index, s_int, p_int, pr, peel_sms(h), al, h->peel_seg);
         if (e == cudaSuccess) e = bt::gather_u64(s_int, h->index.newid, d_sup, m, al);
         if (e == cudaSuccess) e = bt::gather_u32(p_int, h->index.newid, d_phi, m, al);
         if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
@@ -563,7 +566,7 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
         h->last.levels = pr.levels;
         h->last.support_updates = pr.updates;
         h->last.pair_slots = pr.slots;
-        h->last.link_visits = 2 * h->index.w2;
+        h->last.link_visits = h->index.links;
     }
     cudaStreamSynchronize(h->stream);
     return rc;
@@ -690,7 +693,7 @@ static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uin
                               (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, d_sup, al);
     bt::PeelResult pr;
     if (rc == BT_OK && M > 0) {
-        e = bt::peel(h->index, d_sup, d_phi, pr, h->num_sms, al, h->peel_seg);
+        e = bt::peel(h->index, d_sup, d_phi, pr, peel_sms(h), al, h->peel_seg);
         // results back to input order (the edge array is free by now: reuse it)
         uint64_t *g_sup = reinterpret_cast<uint64_t *>(d_edges);
         uint32_t *g_phi = al.get<uint32_t>(M);
@@ -989,7 +992,7 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
                 o.k_init = eps > 0 ? (long long)eps - 1 : 0;
                 o.assign_from = (long long)eps;
                 e = cudaMemsetAsync(phi_local, 0xFF, 4 * hc[0], h->stream);
-                if (e == cudaSuccess) e = bt::peel(ix, sup_c, phi_local, pr, h->num_sms, al, h->peel_seg, &o);
+                if (e == cudaSuccess) e = bt::peel(ix, sup_c, phi_local, pr, peel_sms(h), al, h->peel_seg, &o);
                 if (e == cudaSuccess) e = bt::gather_u32(phi_local, ix.newid, phi_c, hc[0], al);
                 if (e == cudaSuccess) e = bt::settle(cmap, hc[0], cass, phi_c, d_phi, d_asg, al);
                 if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling a candidate subgraph");
@@ -997,6 +1000,8 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
                 else if (pr.status != BT_OK) rc = fail(h, pr.status, "peeling stopped: device barrier timeout or round limit");
             }
             st.wedges += ix.w;
+            st.links += ix.links;
+            if (ix.bytes() > st.index_bytes_max) st.index_bytes_max = ix.bytes();
             bt::free_index(ix, al);
             st.passes++;
             st.rounds += pr.rounds;
@@ -1089,3 +1094,12 @@ int bt_estimate_bytes(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL
 }
 
 }  // extern "C"
+
+namespace bt {
+// Let the handle's peel kernel span 1/ways of the SMs, so that the peels of
+// `ways` handles (server workers) can be resident at once; the kernel is
+// latency-bound, so half the SMs cost the 2M-edge peel about 6 %.
+void share_peel_sms(bt_handle *h, int ways) {
+    if (h && ways > 1) h->peel_sms = h->num_sms / ways > 0 ? h->num_sms / ways : 1;
+}
+}  // namespace bt

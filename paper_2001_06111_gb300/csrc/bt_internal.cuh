@@ -141,15 +141,16 @@ struct Index {
     uint64_t w2 = 0;             // twin pairs (= links / 2)
     uint64_t w = 0;              // priority-obeyed wedges
     uint64_t butterflies = 0;
+    uint64_t links = 0;          // edge-bloom links stored (2 w2, fewer in a compressed index)
     uint32_t *bloom_k = nullptr;     // [nb] bloom numbers
     uint32_t *bloom_off = nullptr;   // [nb+1] first pair of each bloom
     uint2 *pairs = nullptr;          // [w2] (e_uv, e_vw) twin edge ids
     uint32_t *pair_bloom = nullptr;  // [w2]
     uint64_t *inc_off = nullptr;     // [m+1]
-    uint32_t *inc = nullptr;         // [2*w2] pair ids linked to each edge
+    uint32_t *inc = nullptr;         // [links] pair ids linked to each edge
     uint32_t *newid = nullptr;       // [m] input edge id -> internal id (ids above are internal)
     size_t bytes() const {
-        return nb * 8 + 4 + w2 * 12 + (m + 1) * 8 + w2 * 8;
+        return nb * 8 + 4 + w2 * 12 + (m + 1) * 8 + links * 4;
     }
 };
 cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, Alloc &al,
@@ -175,6 +176,10 @@ struct PeelOpts {
 // seg: peel work-item size (32 or 64 entries; anything else means 32)
 cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
                  int num_sms, Alloc &al, int seg = 32, const PeelOpts *opts = nullptr);
+
+// ---------------------------------------------------------------- serving
+// The peel of handle h spans 1/ways of the SMs (server workers share the GPU).
+void share_peel_sms(bt_handle *h, int ways);
 
 // ---------------------------------------------------------------- hierarchy
 // order[i]: edge ids by phi descending, equal phi in ascending id (stable);

@@ -340,13 +340,14 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     BT_CUDA(exclusive_scan_u64(c.w2v, pair_base, n, tot + 1, al));
     BT_CUDA(widen_u32(c.inc_cnt, incc64, m, al));
     BT_CUDA(cudaMemsetAsync(incc64 + m, 0, sizeof(uint64_t), al.stream));
-    BT_CUDA(exclusive_scan_u64(incc64, ix.inc_off, m + 1, nullptr, al));
+    BT_CUDA(exclusive_scan_u64(incc64, ix.inc_off, m + 1, tot + 2, al));
     al.put(incc64);
-    uint64_t h_tot[2];
+    uint64_t h_tot[3];
     BT_CUDA(cudaMemcpyAsync(h_tot, tot, sizeof(h_tot), cudaMemcpyDeviceToHost, stream));
     BT_CUDA(cudaStreamSynchronize(stream));
     ix.nb = h_tot[0];
     ix.w2 = h_tot[1];
+    ix.links = h_tot[2];  // 2 w2, less the links of assigned edges in a compressed index
     if (ix.w2 >= 0xFFFFFFFFull || ix.nb >= 0xFFFFFFFFull) {
         al.put(bloom_base);
         al.put(pair_base);
@@ -357,7 +358,7 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     ix.bloom_off = al.get<uint32_t>(ix.nb + 1);
     ix.pairs = al.get<uint2>(ix.w2);
     ix.pair_bloom = al.get<uint32_t>(ix.w2);
-    ix.inc = al.get<uint32_t>(2 * ix.w2);
+    ix.inc = al.get<uint32_t>(ix.links);
     uint32_t *inc_fill = al.get<uint32_t>(m);
     int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);

@@ -6,6 +6,9 @@
 // one batch (bt_decompose_batch: one disjoint-union pipeline), and complete
 // them.  Requests that arrive while a batch is on the GPU wait for the next
 // free worker; with two or more workers the batches overlap on the device.
+// The peel of each batch is one persistent cooperative kernel, so each
+// worker's peel spans only its share of the SMs: the peels of all workers can
+// then be resident together instead of queuing for the whole GPU.
 // Admission: a request's device footprint is bounded from its degrees in O(m)
 // (priority-obeyed wedges W <= sum over edges of min(d(u), d(v)), Lemma 6;
 // BE-Index bytes grow with W) and the sum over in-flight requests must stay
@@ -178,6 +181,7 @@ int bt_server_create(bt_server **out, int device, const bt_server_config *cfg) {
             delete s;
             return rc;
         }
+        bt::share_peel_sms(h, (int)s->cfg.workers);  // peels of all workers fit on the GPU at once
         s->handles.push_back(h);
     }
     for (uint32_t i = 0; i < s->cfg.workers; ++i)

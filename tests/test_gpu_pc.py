@@ -85,3 +85,28 @@ def test_pc_rejects_bad_tau(h):
         with pytest.raises(bt.BitrussError) as ei:
             bt.bt_decompose_progressive(h, e, 3, 3, tau)
         assert ei.value.code == bt.BT_ERR_ARG
+
+
+@pytest.mark.parametrize("tau", (0.5, 1.0))
+def test_pc_links_of_compressed_indexes(h, tau):
+    # Paper example G: the first pass (eps = k_max = 2) holds the six edges of
+    # support >= 2, K_{3,2} on {u0,u1,u2} x {v0,v1}, one 3-bloom anchored at v1
+    # (highest degree, then id), 3 pairs -> 6 links.  Later passes link only the
+    # unassigned edges: e6..e8 each lie in one butterfly, i.e. one link to a
+    # 2-bloom (support = sum of k_B - 1 over the links, Lemma 3), and e9, e10
+    # in none: 9 links over all passes for both tau.
+    nU, nL, rows = pins.read_golden(os.path.join(GOLDEN, "paper_example_g.txt"))
+    edges = np.array([(int(r[1]), int(r[2])) for r in rows], dtype=np.int32)
+    _, _, st = bt.bt_decompose_progressive(h, edges, nU, nL, tau)
+    assert st["links"] == 9
+    assert st["index_bytes_max"] > 0
+    full = bt.bt_build_index(h, edges, nU, nL)
+    assert st["index_bytes_max"] <= full["index_bytes"] + 8 * 12  # same graph, fewer links
+
+
+def test_pc_compressed_index_smaller_on_medium(h):
+    # the last pass indexes the whole graph but links only unassigned edges
+    g = synth.medium()
+    full = bt.bt_build_index(h, g.edges, g.nU, g.nL)
+    _, _, st = bt.bt_decompose_progressive(h, g.edges, g.nU, g.nL, 0.1)
+    assert 0 < st["index_bytes_max"] < full["index_bytes"]
