@@ -505,6 +505,22 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     e2e_value = job_throughput(ws, m, e2e_steps, e2e_s * 1e3)
 
+    # the k-bitruss hierarchy of the decomposed graph (outside the step): the
+    # order by phi and one H_k, device buffers, CUDA events on the stream
+    phi_u = d_phi.view(torch.uint32) if hasattr(torch, "uint32") else d_phi
+    k_mid = int(d_phi.max().item()) // 2
+    hier = {"order": [], "k_bitruss": []}
+    for _ in range(3):
+        for key, call in (("order", lambda: bt.bt_hierarchy(h, phi_u)),
+                          ("k_bitruss", lambda: bt.bt_k_bitruss(h, phi_u, k_mid))):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            e1.synchronize()
+            hier[key].append(e0.elapsed_time(e1))
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -537,6 +553,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * m,
                 "d2h_bytes_per_step": 12 * m, "steps": e2e_steps},
         "gpu_launches": int(sum(p["launches"] for p in profs)),
+        "hierarchy_ms": {"order_by_phi": statistics.median(hier["order"]),
+                         "k_bitruss": statistics.median(hier["k_bitruss"]), "k": k_mid},
         "clocks": clk,
         "wall_s": wall,
     }
