@@ -246,26 +246,50 @@ __device__ __forceinline__ long long window_top(long long kmin) {
     return kmin + (w < 8 ? 8 : w);
 }
 
-// One kill of a pair of bloom B for round q: count it in C_q(B) and, for the
-// first kill of B in round q, queue B's pairs as bloom items of round q, each
-// recording k_B at the start of round q.
-template <uint32_t kSeg>
-__device__ __forceinline__ void count_kill(const PeelArgs &a, uint32_t B, uint32_t q) {
-    const uint32_t bo0 = a.bloom_off[B], bo1 = a.bloom_off[B + 1];
+// One kill of a pair of bloom B for round q: count it in C_q(B).  Returns
+// true for the first kill of B in round q, with B's first pair, pair count
+// and k_B at the start of round q (its bloom items are then queued).
+__device__ __forceinline__ bool count_kill(const PeelArgs &a, uint32_t B, uint32_t q, uint32_t &bo0,
+                                           uint32_t &span, uint32_t &kB) {
+    bo0 = a.bloom_off[B];
+    const uint32_t bo1 = a.bloom_off[B + 1];
     const unsigned long long w = __ldcg(&a.bw[B]);
     const uint32_t cprev = __ldcg(&a.Cb[(q + 2u) % 3u][B]);  // C_{q-1}(B)
-    if (atomicAdd(&a.Cb[q % 3u][B], 1u) == 0u) {
-        const uint32_t kB = (uint32_t)(w >> 32) == q - 1u ? (uint32_t)w : (uint32_t)w - cprev;
-        const uint32_t span = bo1 - bo0;
-        const uint32_t nseg = (span + kSeg - 1) / kSeg;
-        const uint32_t qb = q & 3u;
-        const uint32_t base = atomicAdd(&a.ctl->n_bseg[qb], nseg);
-        for (uint32_t s = 0; s < nseg; ++s) {
-            const uint32_t left = span - s * kSeg;
-            a.bseg[qb][base + s] =
-                make_uint4(B, bo0 + s * kSeg, (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u), kB);
-        }
+    span = bo1 - bo0;
+    kB = (uint32_t)(w >> 32) == q - 1u ? (uint32_t)w : (uint32_t)w - cprev;
+    return atomicAdd(&a.Cb[q % 3u][B], 1u) == 0u;
+}
+
+// Whole warp (converged): each lane's pairs killed for round q (won[r], bloom
+// B[r]) are counted, and the blooms killed for the first time in round q get
+// their bloom items (one per kSeg pairs, each with k_B at the start of round
+// q).  The warp takes all its item slots with one atomic: in large rounds
+// millions of first kills would otherwise queue on the one counter.
+template <uint32_t kSeg, uint32_t N>
+__device__ __forceinline__ void warp_kills(const PeelArgs &a, uint32_t q, const uint32_t (&B)[N],
+                                           const bool (&won)[N], int lane) {
+    uint32_t bo0[N], span[N], kB[N], nseg[N];
+    uint32_t mine = 0;
+#pragma unroll
+    for (uint32_t r = 0; r < N; ++r) {
+        nseg[r] = 0;
+        if (won[r] && count_kill(a, B[r], q, bo0[r], span[r], kB[r])) nseg[r] = (span[r] + kSeg - 1) / kSeg;
+        mine += nseg[r];
     }
+    const uint32_t incl = dev::warp_incl_scan(mine);
+    const uint32_t all = __shfl_sync(kFull, incl, 31);
+    if (all == 0) return;
+    const uint32_t qb = q & 3u;
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(&a.ctl->n_bseg[qb], all);
+    uint32_t slot = __shfl_sync(kFull, base, 31) + incl - mine;
+#pragma unroll
+    for (uint32_t r = 0; r < N; ++r)
+        for (uint32_t s = 0; s < nseg[r]; ++s, ++slot) {
+            const uint32_t left = span[r] - s * kSeg;
+            a.bseg[qb][slot] =
+                make_uint4(B[r], bo0[r] + s * kSeg, (left < kSeg ? left : kSeg) | (s == 0 ? 0x80000000u : 0u), kB[r]);
+        }
 }
 
 // Edge e joins the batch of round q in a bloom phase: it goes to the block's
@@ -490,15 +514,17 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 const uint32_t i = base + lane * nwarps;
                 const uint4 it = i < n_items ? __ldcg(&a.items[par][i]) : make_uint4(0, 0, 0, 0);
                 const uint32_t cnt = it.w & 0x7FFFFFFFu;
-                if (cnt <= kSmall) {
-                    // this lane's own item: its links' loads and stamps go out together
+                {
+                    // a small item is this lane's own: its links' loads and
+                    // stamps go out together
                     const uint64_t j0 = (uint64_t)it.z << 32 | it.y;
                     uint32_t p[kSmall], B[kSmall];
                     bool won[kSmall];
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r) {
-                        won[r] = r < cnt;
+                        won[r] = cnt <= kSmall && r < cnt;
                         p[r] = won[r] ? a.inc[j0 + r] : 0u;
+                        B[r] = 0;
                     }
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r)
@@ -507,9 +533,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r)
                         if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
-#pragma unroll
-                    for (uint32_t r = 0; r < kSmall; ++r)
-                        if (won[r]) count_kill<kSeg>(a, B[r], round);
+                    warp_kills<kSeg, kSmall>(a, round, B, won, lane);
                 }
                 // items with many links: the whole warp, one item at a time
                 unsigned big = __ballot_sync(kFull, cnt > kSmall);
@@ -526,6 +550,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     for (uint32_t r = 0; r < R; ++r) {
                         won[r] = lane + 32u * r < bcnt;
                         p[r] = won[r] ? a.inc[j0 + 32u * r] : 0u;
+                        B[r] = 0;
                     }
 #pragma unroll
                     for (uint32_t r = 0; r < R; ++r)
@@ -533,9 +558,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 #pragma unroll
                     for (uint32_t r = 0; r < R; ++r)
                         if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
-#pragma unroll
-                    for (uint32_t r = 0; r < R; ++r)
-                        if (won[r]) count_kill<kSeg>(a, B[r], round);
+                    warp_kills<kSeg, R>(a, round, B, won, lane);
                 }
             }
             {
@@ -632,6 +655,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     const uint32_t x = threadIdx.x + r * (uint32_t)kPeelThreads;
                     won[r] = false;
                     p[r] = 0;
+                    B[r] = 0;
                     if (x < lim) {
                         const uint32_t j = dev::last_le_u32(s_joff, nj, x);
                         if (s_joff[j] + s_jd[j] <= kBlockLinks) {
@@ -647,9 +671,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 #pragma unroll
                 for (uint32_t r = 0; r < 2; ++r)
                     if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, q) == kAlive;
-#pragma unroll
-                for (uint32_t r = 0; r < 2; ++r)
-                    if (won[r]) count_kill<kSeg>(a, B[r], q);
+                warp_kills<kSeg, 2>(a, q, B, won, lane);
                 if (threadIdx.x == 0) s_jn = 0;
             }
         }
