@@ -66,6 +66,8 @@ constexpr uint32_t kErrBarrier = 1u;
 constexpr uint32_t kErrRounds = 2u;
 constexpr uint32_t kErrPeelOverflow = 4u;
 constexpr unsigned kFull = 0xffffffffu;
+// level-jump windows above this size queue their batch with warp-aggregated atomics
+constexpr uint32_t kWarpSlotsMin = 1u << 16;
 
 struct Ctl {
     unsigned long long bar_count;  // barrier arrivals (monotonic within a launch)
@@ -456,10 +458,23 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 L.khi = window_top((long long)mn);
                 ap ^= 1u;
                 if (gtid == 0) ctl->n_alive[ap ^ 1u] = 0;
-                // W2: list every alive edge below the new window top
-                for (uint32_t i = gtid; i < v_alive; i += nthreads) {
-                    const uint32_t e = ldcg_u32(&a.alive[ap][i]);
-                    if (ldcg_ll(&a.sup[e]) < L.khi) push_near(a, e, L.nq);
+                // W2: list every alive edge below the new window top (one
+                // counter atomic per warp: the list can take most edges)
+                for (uint32_t i0 = gwarp * 32u; i0 < v_alive; i0 += nthreads) {
+                    const uint32_t i = i0 + lane;
+                    uint32_t e = 0;
+                    bool keep = false;
+                    if (i < v_alive) {
+                        e = ldcg_u32(&a.alive[ap][i]);
+                        keep = ldcg_ll(&a.sup[e]) < L.khi;
+                    }
+                    const unsigned int mask = __ballot_sync(kFull, keep);
+                    if (mask) {
+                        unsigned int base = 0;
+                        if (lane == 0) base = atomicAdd(&ctl->n_near[L.nq], (unsigned)__popc(mask));
+                        base = __shfl_sync(kFull, base, 0);
+                        if (keep) a.near[L.nq][base + __popc(mask & ((1u << lane) - 1u))] = e;
+                    }
                 }
                 if (gtid == 0) atomicAdd(&ctl->windows, 1ull);
                 {
@@ -475,14 +490,49 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 break;
             }
             // L2: the batch is every window edge with support <= k; their
-            // links become incidence items of this round
+            // links become incidence items of this round.  A large window
+            // (a level can select millions of edges) takes its item slots
+            // with one atomic per warp; a small one per edge, which is faster
+            // when only a few edges are selected.
             uint32_t sel = 0;
-            for (uint32_t i = gtid; i < v_near; i += nthreads) {
-                const uint32_t e = ldcg_u32(&a.near[L.nq][i]);
-                if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k) {
-                    join_batch(a, e, round, L.k);
-                    push_items<kSeg>(a, e, par, a.inc_off[e], a.inc_off[e + 1]);
-                    ++sel;
+            if (v_near > kWarpSlotsMin) {
+                for (uint32_t i0 = gwarp * 32u; i0 < v_near; i0 += nthreads) {
+                    const uint32_t i = i0 + lane;
+                    uint32_t e = 0, nseg = 0;
+                    uint64_t ib = 0, ie = 0;
+                    if (i < v_near) {
+                        e = ldcg_u32(&a.near[L.nq][i]);
+                        if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k) {
+                            join_batch(a, e, round, L.k);
+                            ++sel;
+                            ib = a.inc_off[e];
+                            ie = a.inc_off[e + 1];
+                            nseg = (uint32_t)((ie - ib + kSeg - 1) / kSeg);
+                        }
+                    }
+                    const uint32_t incl = dev::warp_incl_scan(nseg);
+                    const uint32_t all = __shfl_sync(kFull, incl, 31);
+                    if (all) {
+                        uint32_t base = 0;
+                        if (lane == 31) base = atomicAdd(&ctl->n_items[par], all);
+                        uint32_t slot = __shfl_sync(kFull, base, 31) + incl - nseg;
+                        for (uint32_t s2 = 0; s2 < nseg; ++s2, ++slot) {
+                            const uint64_t j = ib + (uint64_t)s2 * kSeg;
+                            const uint64_t left = ie - j;
+                            const uint32_t cnt = (uint32_t)(left < kSeg ? left : kSeg);
+                            a.items[par][slot] =
+                                make_uint4(e, (uint32_t)j, (uint32_t)(j >> 32), cnt | (s2 == 0 ? 0x80000000u : 0u));
+                        }
+                    }
+                }
+            } else {
+                for (uint32_t i = gtid; i < v_near; i += nthreads) {
+                    const uint32_t e = ldcg_u32(&a.near[L.nq][i]);
+                    if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k) {
+                        join_batch(a, e, round, L.k);
+                        push_items<kSeg>(a, e, par, a.inc_off[e], a.inc_off[e + 1]);
+                        ++sel;
+                    }
                 }
             }
             sel = dev::warp_sum(sel);
