@@ -367,6 +367,7 @@ def serve_trace(srv, pool, big, rate, seconds, seed):
         lat.append(info["latency_seconds"])
         ok += info["status"] == 0
     span = time.perf_counter() - t0
+    serve_trace.last_big = np.array([g.m >= 1_000_000 for g in picks])
     return np.array(lat), span, ok, len(t_arr), sum(g.m for g in picks)
 
 
@@ -390,16 +391,24 @@ def run_serve(args):
         for i, rate in enumerate(W["rates"]):
             lat, span, ok, n, edges = serve_trace(srv, pool, big, rate, W["seconds"], 1000 + i)
             st = srv.stats()
+            isbig = serve_trace.last_big
             sweep.append({"rate": rate, "requests": n, "ok": ok, "throughput_req_s": n / span,
                           "edges_per_s": edges / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                           "p99_ms": float(np.percentile(lat, 99) * 1e3), "span_s": span,
-                          "batches_total": st["batches"], "max_batch": st["max_batch_graphs"]})
+                          "batches_total": st["batches"], "max_batch": st["max_batch_graphs"],
+                          "small_p50_ms": float(np.percentile(lat[~isbig], 50) * 1e3) if (~isbig).any() else None,
+                          "small_p99_ms": float(np.percentile(lat[~isbig], 99) * 1e3) if (~isbig).any() else None,
+                          "large_p50_ms": float(np.percentile(lat[isbig], 50) * 1e3) if isbig.any() else None,
+                          "large_requests": int(isbig.sum())})
             print(json.dumps({"serve_rate": sweep[-1]}), flush=True)
     with bt.Server(0, workers=1, max_batch_graphs=1) as plain:
         lat, span, ok, n, edges = serve_trace(plain, pool, big, W["rates"][0], W["seconds"], 1000)
+        isbig = serve_trace.last_big
         plain_res = {"rate": W["rates"][0], "requests": n, "ok": ok, "throughput_req_s": n / span,
                      "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                     "p99_ms": float(np.percentile(lat, 99) * 1e3), "span_s": span}
+                     "p99_ms": float(np.percentile(lat, 99) * 1e3), "span_s": span,
+                     "small_p50_ms": float(np.percentile(lat[~isbig], 50) * 1e3) if (~isbig).any() else None,
+                     "large_p50_ms": float(np.percentile(lat[isbig], 50) * 1e3) if isbig.any() else None}
     best = max(sweep, key=lambda r: r["throughput_req_s"])
     line = {"metric": "served req/s, p50/p99 ms", "value": best["throughput_req_s"], "unit": "req/s",
             "n_gpus": 1, "higher_is_better": True, "vs_baseline": None, "dtype": "int64",
@@ -420,9 +429,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS),
                     help="medium (default) is the benchmark workload; small is for profiling")
+    ap.add_argument("--rates", default="",
+                    help="serve workload: comma-separated arrival rates (req/s) instead of the full sweep")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
+    if args.workload == "serve" and args.rates:
+        WORKLOAD = dict(WORKLOAD, rates=[float(r) for r in args.rates.split(",")])
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

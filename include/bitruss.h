@@ -331,6 +331,12 @@ int bt_k_bitruss(bt_handle *h, const uint32_t *phi, uint64_t m, uint32_t k, uint
  * batch, and with several workers batches overlap on the device.  Admission
  * uses an O(m) upper bound on a request's device bytes from its degrees
  * (priority-obeyed wedges <= sum over edges of min(d(u), d(v)), Lemma 6).
+ * Large requests (config large_edges) are never batched with others, and
+ * with several workers one of them serves the small requests first (passing
+ * waiting large ones), so a large graph does not hold back the small requests
+ * that arrive behind it; the other workers take the oldest large request
+ * first.  Each worker falls back to the other kind when its own has none
+ * waiting, so neither kind starves; within a kind, first come, first served.
  * Results are exactly those of bt_decompose on the graph alone. */
 typedef struct bt_server bt_server;
 
@@ -339,7 +345,10 @@ typedef struct {
     uint32_t workers;              /* concurrent batches; 0 = 2 */
     uint32_t max_batch_graphs;     /* 0 = unlimited; 1 = one request at a time (plain serial) */
     uint32_t flags;                /* 0 or BT_TIE_LOWER_FIRST */
-    uint32_t reserved;
+    uint32_t large_edges;          /* a request with at least this many edges runs in a batch of its
+                                      own; with several workers the last one serves small requests
+                                      first and the others large ones first; 0 = 2^20,
+                                      UINT32_MAX = no request counts as large */
 } bt_server_config;
 
 typedef struct {

@@ -102,7 +102,7 @@ class PcStats(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("workers", ctypes.c_uint32),
                 ("max_batch_graphs", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("large_edges", ctypes.c_uint32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -370,9 +370,9 @@ class Server:
     request keeps its edge array and outputs alive until it completes."""
 
     def __init__(self, device: int = 0, memory_budget_bytes: int = 0, workers: int = 0,
-                 max_batch_graphs: int = 0, flags: int = 0):
+                 max_batch_graphs: int = 0, flags: int = 0, large_edges: int = 0):
         lib = load()
-        cfg = ServerConfig(memory_budget_bytes, workers, max_batch_graphs, flags, 0)
+        cfg = ServerConfig(memory_budget_bytes, workers, max_batch_graphs, flags, large_edges)
         p = ctypes.c_void_p()
         rc = lib.bt_server_create(ctypes.byref(p), device, ctypes.byref(cfg))
         if rc != BT_OK:

@@ -6,6 +6,9 @@
 // one batch (bt_decompose_batch: one disjoint-union pipeline), and complete
 // them.  Requests that arrive while a batch is on the GPU wait for the next
 // free worker; with two or more workers the batches overlap on the device.
+// A large request runs alone; one worker serves small requests first and
+// the others large ones first (see the admission code), so small requests do
+// not wait behind a large graph.
 // The peel of each batch is one persistent cooperative kernel, so each
 // worker's peel spans only its share of the SMs: the peels of all workers can
 // then be resident together instead of queuing for the whole GPU.
@@ -97,23 +100,63 @@ struct bt_server {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return stop || !queue.empty(); });
                 if (queue.empty() && stop) break;
-                // admit from the head, FIFO, while the budget allows
-                while (!queue.empty()) {
-                    Request *r = queue.front();
-                    if (r->bytes > cfg.memory_budget_bytes) {  // can never fit
-                        queue.pop_front();
-                        r->status = BT_ERR_NOMEM;
-                        r->t_done = now_s();
-                        stats.rejected++;
-                        stats.completed++;
-                        cv_done.notify_all();
+                // requests that can never fit are rejected first
+                for (auto it = queue.begin(); it != queue.end();) {
+                    Request *r = *it;
+                    if (r->bytes <= cfg.memory_budget_bytes) {
+                        ++it;
                         continue;
                     }
-                    if (in_flight_bytes + bytes + r->bytes > cfg.memory_budget_bytes) break;
-                    if (cfg.max_batch_graphs && batch.size() >= cfg.max_batch_graphs) break;
-                    queue.pop_front();
-                    bytes += r->bytes;
-                    batch.push_back(r);
+                    it = queue.erase(it);
+                    r->status = BT_ERR_NOMEM;
+                    r->t_done = now_s();
+                    stats.rejected++;
+                    stats.completed++;
+                    cv_done.notify_all();
+                }
+                // A large request (>= large_edges edges) runs alone.  One
+                // worker: queue order.  Several: worker 0 takes the oldest
+                // large request first, the last worker the small ones first
+                // (passing large ones), the others as worker 0; each falls
+                // back to the other kind when its own has none waiting.
+                const auto is_large = [&](const Request *r) { return r->g.m >= cfg.large_edges; };
+                const auto fits = [&](const Request *r) {
+                    return in_flight_bytes + bytes + r->bytes <= cfg.memory_budget_bytes;
+                };
+                const auto take_large = [&]() {
+                    for (auto it = queue.begin(); it != queue.end(); ++it)
+                        if (is_large(*it)) {
+                            if (!fits(*it)) return false;  // the oldest large one waits for memory
+                            bytes += (*it)->bytes;
+                            batch.push_back(*it);
+                            queue.erase(it);
+                            return true;
+                        }
+                    return false;
+                };
+                const auto take_small = [&](bool stop_at_large) {
+                    for (auto it = queue.begin(); it != queue.end();) {
+                        Request *r = *it;
+                        if (is_large(r)) {
+                            if (stop_at_large) break;
+                            ++it;
+                            continue;
+                        }
+                        if (!fits(r)) break;
+                        if (cfg.max_batch_graphs && batch.size() >= cfg.max_batch_graphs) break;
+                        it = queue.erase(it);
+                        bytes += r->bytes;
+                        batch.push_back(r);
+                    }
+                    return !batch.empty();
+                };
+                if (cfg.workers == 1) {
+                    if (!queue.empty() && is_large(queue.front())) take_large();
+                    else take_small(true);
+                } else if (wi == (int)cfg.workers - 1) {
+                    if (!take_small(false)) take_large();
+                } else {
+                    if (!take_large()) take_small(false);
                 }
                 if (batch.empty()) {
                     // the head waits for memory held by other workers
@@ -169,6 +212,7 @@ int bt_server_create(bt_server **out, int device, const bt_server_config *cfg) {
     if (cfg) s->cfg = *cfg;
     if (!s->cfg.memory_budget_bytes) s->cfg.memory_budget_bytes = 120ull << 30;
     if (!s->cfg.workers) s->cfg.workers = 2;
+    if (!s->cfg.large_edges) s->cfg.large_edges = 1u << 20;
     if (s->cfg.flags & ~(uint32_t)BT_TIE_LOWER_FIRST) {
         delete s;
         return BT_ERR_ARG;

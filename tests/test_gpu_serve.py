@@ -53,3 +53,20 @@ def test_admission_rejects_oversized_request():
         info, _ = srv.poll(rid, wait=True)
         assert info["status"] == bt.BT_ERR_NOMEM
         assert srv.stats()["rejected"] == 1
+
+
+def test_large_requests_alone_small_ones_pass(alone):
+    # threshold 30k edges: two large graphs, then small ones.  Large requests
+    # run in batches of their own, the small-first worker takes the small ones
+    # while the large ones run, and every result is exact.
+    large = [synth.vertex_sample(synth.medium(), 0.3, s) for s in (5, 6)]
+    small = [synth.batch_graph(200 + i, hi=20000) for i in range(20)]
+    assert all(g.m >= 30000 for g in large) and all(g.m < 30000 for g in small)
+    with bt.Server(0, workers=2, large_edges=30000) as srv:
+        ids = [srv.submit(g.edges, g.nU, g.nL) for g in large + small]
+        res = [srv.poll(i, wait=True) for i in ids]
+        st = srv.stats()
+    assert st["completed"] == 22 and st["batches"] >= 3
+    for (info, (_, phi)), g in zip(res, large + small):
+        assert info["status"] == bt.BT_OK
+        np.testing.assert_array_equal(phi, alone(g.edges, g.nU, g.nL)[1])
