@@ -336,7 +336,8 @@ int bt_k_bitruss(bt_handle *h, const uint32_t *phi, uint64_t m, uint32_t k, uint
  * waiting large ones), so a large graph does not hold back the small requests
  * that arrive behind it; the other workers take the oldest large request
  * first.  Each worker falls back to the other kind when its own has none
- * waiting, so neither kind starves; within a kind, first come, first served.
+ * waiting (the small-first worker only when two or more large requests
+ * wait), so neither kind starves; within a kind, first come, first served.
  * Results are exactly those of bt_decompose on the graph alone. */
 typedef struct bt_server bt_server;
 

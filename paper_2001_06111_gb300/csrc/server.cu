@@ -118,7 +118,8 @@ struct bt_server {
                 // worker: queue order.  Several: worker 0 takes the oldest
                 // large request first, the last worker the small ones first
                 // (passing large ones), the others as worker 0; each falls
-                // back to the other kind when its own has none waiting.
+                // back to the other kind when its own has none waiting (the
+                // last worker only when two or more large requests wait).
                 const auto is_large = [&](const Request *r) { return r->g.m >= cfg.large_edges; };
                 const auto fits = [&](const Request *r) {
                     return in_flight_bytes + bytes + r->bytes <= cfg.memory_budget_bytes;
@@ -154,7 +155,13 @@ struct bt_server {
                     if (!queue.empty() && is_large(queue.front())) take_large();
                     else take_small(true);
                 } else if (wi == (int)cfg.workers - 1) {
-                    if (!take_small(false)) take_large();
+                    // it helps with large requests only when two or more
+                    // wait, so that one worker usually stays free for small ones
+                    if (!take_small(false)) {
+                        int waiting = 0;
+                        for (const Request *r : queue) waiting += is_large(r) ? 1 : 0;
+                        if (waiting >= 2) take_large();
+                    }
                 } else {
                     if (!take_large()) take_small(false);
                 }
@@ -172,13 +179,19 @@ struct bt_server {
             graphs.clear();
             const double t0 = now_s();
             for (Request *r : batch) graphs.push_back(r->g);
+            // fixed schedules: the batch autotuner would time candidates on
+            // the request path whenever a new batch shape appears
+            bt_tune tune{};
+            const bool alone_large = batch.size() == 1 && batch[0]->g.m >= cfg.large_edges;
+            tune.count_threads = alone_large ? 512 : 256;
+            tune.peel_item = 32;
             bt_batch_stats bs{};
-            rc = bt_decompose_batch(h, graphs.data(), (uint32_t)graphs.size(), nullptr, &bs,
+            rc = bt_decompose_batch(h, graphs.data(), (uint32_t)graphs.size(), &tune, &bs,
                                     cfg.flags & BT_TIE_LOWER_FIRST);
             if (rc != BT_OK && graphs.size() > 1) {
                 // isolate the failing request(s): retry one by one
                 for (size_t i = 0; i < batch.size(); ++i)
-                    batch[i]->status = bt_decompose_batch(h, &graphs[i], 1, nullptr, nullptr,
+                    batch[i]->status = bt_decompose_batch(h, &graphs[i], 1, &tune, nullptr,
                                                           cfg.flags & BT_TIE_LOWER_FIRST);
             } else {
                 for (Request *r : batch) r->status = rc;
