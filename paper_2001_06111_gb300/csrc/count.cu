@@ -213,6 +213,8 @@ __global__ void __launch_bounds__(NT) k_emit(
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 uint32_t w = adj[arc];
                 uint32_t c = ld_cg(&cnt[w]);
+                // a single wedge is the only reader of its counter: clear it now
+                if (c == 1u) cnt[w] = 0u;
                 if (c >= 2 && atomicCAS(&aux[w], 0u, 1u) == 0u) {
                     unsigned long long old = atomicAdd(&s_alloc, (1ull << 32) | c);
                     uint32_t j = (uint32_t)(old >> 32);
@@ -236,6 +238,9 @@ __global__ void __launch_bounds__(NT) k_emit(
                 if (x >= 2) {
                     uint64_t B = bb + (x - 2);
                     uint32_t pos = atomicSub(&cnt[w], 1u) - 1u;
+                    // the last wedge of the bloom comes after every read of
+                    // aux[w] (each precedes its own decrement): clear it
+                    if (pos == 0u) aux[w] = 0u;
                     uint32_t slot = ld_cg(&bloom_off[B]) + pos;
                     uint32_t euv = ch.e[vi], evw = eid[arc];
                     const bool fu = assigned && assigned[euv], fw = assigned && assigned[evw];
@@ -251,18 +256,6 @@ __global__ void __launch_bounds__(NT) k_emit(
                         inc[inc_off[evw] + q2] = slot;
                     }
                 }
-            }
-            __syncthreads();
-        }
-        // reset: blooms already drained cnt to zero; clear aux and single wedges
-        for (uint32_t c0 = 0; c0 < h; c0 += NT) {
-            uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
-            for (uint32_t t = threadIdx.x; t < T; t += NT) {
-                uint32_t vi;
-                uint64_t arc = wedge_arc(ch, off, t, vi);
-                uint32_t w = adj[arc];
-                if (ld_cg(&aux[w]) == 0u) cnt[w] = 0u;
-                else aux[w] = 0u;
             }
             __syncthreads();
         }
