@@ -29,6 +29,7 @@ struct bt_handle {
     int count_nt = 512;   // schedule used by the next pipeline run
     int peel_seg = 32;
     int peel_sms = 0;     // SMs the peel kernel spans (0: all); a server worker takes its share
+    const bt::GraphSplit *split = nullptr;  // graphs of the batch union being prepared, if any
     std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (count_nt, peel_seg)
     unsigned char *pinned = nullptr;  // page-locked staging for batch copies
     size_t pinned_bytes = 0;
@@ -136,7 +137,7 @@ int prepare(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_
         P.d_edges = P.owned;
     }
     cudaError_t e = cudaMemsetAsync(h->err_word, 0, sizeof(uint32_t), h->stream);
-    if (e == cudaSuccess) e = bt::build_csr(P.d_edges, m, nU, nL, flags, P.g, h->err_word, al);
+    if (e == cudaSuccess) e = bt::build_csr(P.d_edges, m, nU, nL, flags, P.g, h->err_word, al, h->split);
     if (e != cudaSuccess) return cuda_fail(h, e, "building the CSR");
     uint32_t hw = 0;
     e = cudaMemcpyAsync(&hw, h->err_word, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream);
@@ -688,9 +689,19 @@ static int decompose_union(bt_handle *h, const bt_graph *graphs, uint32_t n, uin
         else if (hw[0] & bt::kErrRange)
             rc = fail(h, BT_ERR_RANGE, "graph %u of the batch has a vertex id outside its layers", hw[1]);
     }
-    if (rc == BT_OK && M > 0)
+    if (rc == BT_OK && M > 0) {
+        // rank the union graph by graph: the counting kernels then size their
+        // per-block counters by the largest graph instead of the union
+        bt::GraphSplit split;
+        split.ng = n;
+        split.offU = d_tab;
+        split.offL = d_tab + n;
+        for (uint32_t g = 0; g < n; ++g) split.max_n = std::max(split.max_n, gnU[g] + gnL[g]);
+        h->split = &split;
         rc = build_index_impl(h, d_edges, M, (uint32_t)NU, (uint32_t)NL,
                               (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, d_sup, al);
+        h->split = nullptr;
+    }
     bt::PeelResult pr;
     if (rc == BT_OK && M > 0) {
         e = bt::peel(h->index, d_sup, d_phi, pr, peel_sms(h), al, h->peel_seg);
@@ -1086,7 +1097,9 @@ int bt_estimate_bytes(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL
     // index bound of 16 bytes per wedge plus per-bloom records (<= W/2 blooms)
     uint64_t csr = (n + 1) * 8 + 2 * m * (4 + 4 + 4) + n * 12;
     uint64_t sort_scratch = 2 * m * 24;
-    uint64_t counters = 2ull * 152 * 2 * n * 4;
+    // two u32 counters per vertex for every resident count block (at most
+    // 152 SMs x 2048 threads / 256-thread blocks)
+    uint64_t counters = 2ull * 4 * n * (152ull * 2048 / 256);
     uint64_t edges_b = m * (8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4);
     uint64_t index_b = W * (8 + 4 + 8 + 1) + (W / 2 + 1) * 16;
     *bytes_out = csr + std::max(sort_scratch, counters) + edges_b + index_b + (1ull << 20);

@@ -101,12 +101,28 @@ struct Csr {
     // contiguous (blooms anchored there touch neighbouring words).  eid holds
     // internal ids; newid maps input id -> internal id.
     uint32_t *newid = nullptr;  // [m]
+    // A disjoint union of graphs is ranked graph by graph (each graph's own
+    // degree-then-id order, graph after graph), so the wedges of a start
+    // vertex stay inside its graph: vbase[r] is the first rank of r's graph,
+    // and the counting kernels index their per-block counters by w - vbase[u],
+    // cnt_n entries each (the largest graph) instead of n.
+    uint32_t *vbase = nullptr;  // [n], or null for one graph
+    uint32_t cnt_n = 0;
+};
+
+// The graphs of a disjoint union (bt_decompose_batch): offU/offL (device,
+// ng entries) are each graph's first upper / lower id in the union; max_n
+// the largest nU + nL.
+struct GraphSplit {
+    uint32_t ng = 0;
+    const uint32_t *offU = nullptr, *offL = nullptr;
+    uint32_t max_n = 0;
 };
 
 // Builds the CSR (and wedge prefix lengths) from a device edge list.
 // err_word: device u32 receiving kErr* bits.  Returns a CUDA error.
 cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
-                      Csr &g, uint32_t *err_word, Alloc &al);
+                      Csr &g, uint32_t *err_word, Alloc &al, const GraphSplit *split = nullptr);
 void free_csr(Csr &g, Alloc &al);
 // out[e] = in[newid[e]]: a per-edge array in internal order back to input order.
 cudaError_t gather_u64(const uint64_t *in, const uint32_t *newid, uint64_t *out, uint64_t m, Alloc &al);

@@ -78,13 +78,13 @@ __device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p);
 template <int NT>
 __device__ void pass_count(Chunk<NT> &ch, const uint64_t *off, const uint32_t *adj,
                            const uint32_t *eid, const uint32_t *pl, uint64_t a, uint32_t h,
-                           uint32_t *cnt) {
+                           uint32_t *cnt, uint32_t vb) {
     for (uint32_t c0 = 0; c0 < h; c0 += NT) {
         uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
         for (uint32_t t = threadIdx.x; t < T; t += NT) {
             uint32_t vi;
             uint64_t arc = wedge_arc(ch, off, t, vi);
-            atomicAdd(&cnt[adj[arc]], 1u);
+            atomicAdd(&cnt[adj[arc] - vb], 1u);
         }
         __syncthreads();
     }
@@ -95,13 +95,16 @@ __global__ void __launch_bounds__(NT) k_count(
     const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
     const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
     const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
+    const uint32_t *__restrict__ vbase, uint32_t cn,
     uint32_t *cnt_all, unsigned long long *support, uint32_t *inc_cnt, uint64_t *w2v,
     uint64_t *nbv, unsigned long long *totals, uint32_t *queue, const uint8_t *__restrict__ assigned) {
     __shared__ Chunk<NT> ch;
     __shared__ unsigned long long s_acc[NT];
     __shared__ uint32_t s_inc[NT];
     __shared__ uint32_t s_q;
-    uint32_t *cnt = cnt_all + (size_t)blockIdx.x * n;
+    // this block's counters: the w of a start vertex u lie in u's graph, at
+    // w - vbase[u] (vbase null: one graph)
+    uint32_t *cnt = cnt_all + (size_t)blockIdx.x * cn;
     s_acc[threadIdx.x] = 0;
     s_inc[threadIdx.x] = 0;
     unsigned long long bf_total = 0;
@@ -117,7 +120,8 @@ __global__ void __launch_bounds__(NT) k_count(
         }
         const uint64_t a = off[u];
         const uint32_t h = hv[u];
-        pass_count(ch, off, adj, eid, pl, a, h, cnt);
+        const uint32_t vb = vbase ? vbase[u] : 0u;
+        pass_count(ch, off, adj, eid, pl, a, h, cnt, vb);
         // pass B: attribute c-1 to both edges of every wedge in a bloom
         unsigned long long w2_local = 0;
         for (uint32_t c0 = 0; c0 < h; c0 += NT) {
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(NT) k_count(
             for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
-                uint32_t c = ld_cg(&cnt[adj[arc]]);
+                uint32_t c = ld_cg(&cnt[adj[arc] - vb]);
                 if (c >= 2) {
                     uint32_t evw = eid[arc];
                     atomicAdd(&support[evw], (unsigned long long)(c - 1));
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(NT) k_count(
             for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
-                uint32_t old = atomicExch(&cnt[adj[arc]], 0u);
+                uint32_t old = atomicExch(&cnt[adj[arc] - vb], 0u);
                 if (old >= 2) {
                     ++nb_local;
                     bf_total += (unsigned long long)old * (old - 1) / 2;
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(NT) k_emit(
     const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
     const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
     const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
+    const uint32_t *__restrict__ vbase, uint32_t cn,
     uint32_t *cnt_all, uint32_t *aux_all, const uint64_t *__restrict__ bloom_base,
     const uint64_t *__restrict__ pair_base, const uint64_t *__restrict__ inc_off,
     uint32_t *inc_fill, uint32_t *bloom_k, uint32_t *bloom_off, uint2 *pairs,
@@ -193,8 +198,8 @@ __global__ void __launch_bounds__(NT) k_emit(
     // bloom count (high 32 bits) and pair count (low 32 bits) of the vertex,
     // advanced by one atomic so that pair ranges follow bloom ids
     __shared__ unsigned long long s_alloc;
-    uint32_t *cnt = cnt_all + (size_t)blockIdx.x * n;
-    uint32_t *aux = aux_all + (size_t)blockIdx.x * n;
+    uint32_t *cnt = cnt_all + (size_t)blockIdx.x * cn;
+    uint32_t *aux = aux_all + (size_t)blockIdx.x * cn;
     for (;;) {
         uint32_t u = next_vertex(queue, n, &s_q);
         if (u == 0xFFFFFFFFu) break;
@@ -203,15 +208,16 @@ __global__ void __launch_bounds__(NT) k_emit(
         const uint32_t h = hv[u];
         const uint64_t bb = bloom_base[u];
         const uint64_t pb = pair_base[u];
+        const uint32_t vb = vbase ? vbase[u] : 0u;
         if (threadIdx.x == 0) s_alloc = 0;
-        pass_count(ch, off, adj, eid, pl, a, h, cnt);
+        pass_count(ch, off, adj, eid, pl, a, h, cnt, vb);
         // claim: one thread per bloom allocates its id and pair range
         for (uint32_t c0 = 0; c0 < h; c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
             for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
-                uint32_t w = adj[arc];
+                const uint32_t w = adj[arc] - vb;  // counter index
                 uint32_t c = ld_cg(&cnt[w]);
                 // a single wedge is the only reader of its counter: clear it now
                 if (c == 1u) cnt[w] = 0u;
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(NT) k_emit(
             for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
-                uint32_t w = adj[arc];
+                const uint32_t w = adj[arc] - vb;  // counter index
                 uint32_t x = ld_cg(&aux[w]);
                 if (x >= 2) {
                     uint64_t B = bb + (x - 2);
@@ -278,10 +284,10 @@ template <int NT>
 void launch_count(bool index, unsigned blocks, const Csr &g, uint32_t *cnt, unsigned long long *sup,
                   CountOut &o, unsigned long long *totals, uint32_t *queue, cudaStream_t st) {
     if (index)
-        k_count<true, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, cnt, sup,
+        k_count<true, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, g.vbase, g.cnt_n, cnt, sup,
                                                   o.inc_cnt, o.w2v, o.nbv, totals, queue, o.assigned);
     else
-        k_count<false, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, cnt, sup,
+        k_count<false, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, g.vbase, g.cnt_n, cnt, sup,
                                                    nullptr, nullptr, nullptr, totals, queue, nullptr);
 }
 
@@ -293,11 +299,11 @@ cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int 
     if (nt != 256 && nt != 1024) nt = 512;
     int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
-    uint32_t *cnt = al.get<uint32_t>((size_t)blocks * n);
+    uint32_t *cnt = al.get<uint32_t>((size_t)blocks * g.cnt_n);
     uint32_t *queue = al.get<uint32_t>(1);
     unsigned long long *totals = al.get<unsigned long long>(1);
     if (al.err != cudaSuccess) return al.err;
-    BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)blocks * n, al.stream));
+    BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)blocks * g.cnt_n, al.stream));
     BT_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), al.stream));
     BT_CUDA(cudaMemsetAsync(totals, 0, sizeof(unsigned long long), al.stream));
     BT_CUDA(cudaMemsetAsync(o.support, 0, sizeof(uint64_t) * g.m, al.stream));
@@ -355,20 +361,20 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     uint32_t *inc_fill = al.get<uint32_t>(m);
     int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
-    uint32_t *cnt = al.get<uint32_t>((size_t)blocks * n);
-    uint32_t *aux = al.get<uint32_t>((size_t)blocks * n);
+    uint32_t *cnt = al.get<uint32_t>((size_t)blocks * g.cnt_n);
+    uint32_t *aux = al.get<uint32_t>((size_t)blocks * g.cnt_n);
     uint32_t *queue = al.get<uint32_t>(1);
     if (al.err != cudaSuccess) return al.err;
     uint32_t w2_32 = (uint32_t)ix.w2;
     BT_CUDA(cudaMemcpyAsync(ix.bloom_off + ix.nb, &w2_32, sizeof(uint32_t), cudaMemcpyHostToDevice,
                             stream));
     BT_CUDA(cudaMemsetAsync(inc_fill, 0, sizeof(uint32_t) * m, al.stream));
-    BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)blocks * n, al.stream));
-    BT_CUDA(cudaMemsetAsync(aux, 0, sizeof(uint32_t) * (size_t)blocks * n, al.stream));
+    BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)blocks * g.cnt_n, al.stream));
+    BT_CUDA(cudaMemsetAsync(aux, 0, sizeof(uint32_t) * (size_t)blocks * g.cnt_n, al.stream));
     BT_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), al.stream));
     al.mark(kPhEmit, false);
 #define BT_EMIT_ARGS                                                                         \
-    g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, cnt, aux, bloom_base, pair_base, ix.inc_off,  \
+    g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, g.vbase, g.cnt_n, cnt, aux, bloom_base, pair_base, ix.inc_off,  \
         inc_fill, ix.bloom_k, ix.bloom_off, ix.pairs, ix.pair_bloom, ix.inc, queue, c.assigned
     if (nt == 256) k_emit<256><<<blocks, 256, 0, al.stream>>>(BT_EMIT_ARGS);
     else if (nt == 1024) k_emit<1024><<<blocks, 1024, 0, al.stream>>>(BT_EMIT_ARGS);

@@ -51,6 +51,43 @@ __global__ void k_rank(const uint32_t *order, const uint32_t *deg_sorted, uint32
     }
 }
 
+// Union ranking key of every vertex id: its graph, then its degree (the sort
+// is stable, so ties stay in id order, as for the graph alone).
+__global__ void k_graph_keys(const uint32_t *deg, uint32_t n, uint32_t nU, uint32_t nL, uint32_t flags,
+                             uint32_t ng, const uint32_t *offU, const uint32_t *offL, int dbits,
+                             uint32_t *keys) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        // the layer and layer-local id of x (see gids)
+        bool upper;
+        uint32_t loc;
+        if (flags & BT_TIE_LOWER_FIRST) {
+            upper = x < nU;
+            loc = upper ? x : x - nU;
+        } else {
+            upper = x >= nL;
+            loc = upper ? x - nL : x;
+        }
+        const uint32_t *off = upper ? offU : offL;
+        uint32_t lo = 0, hi = ng;  // largest g with off[g] <= loc
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= loc) lo = mid; else hi = mid;
+        }
+        keys[x] = lo << dbits | deg[x];
+    }
+}
+
+// After the union sort: rank r's degree and the first rank of its graph.
+__global__ void k_graph_rank(const uint32_t *keys_sorted, uint32_t n, int dbits, const uint32_t *offU,
+                             const uint32_t *offL, uint32_t *deg_sorted, uint32_t *vbase) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const uint32_t k = keys_sorted[r];
+        const uint32_t gi = k >> dbits;
+        deg_sorted[r] = k & ((1u << dbits) - 1u);
+        vbase[r] = offU[gi] + offL[gi];  // vertices of the graphs before it
+    }
+}
+
 __global__ void k_arcs(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
                        const uint32_t *rank, uint32_t n, uint64_t *keys, uint32_t *vals) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
@@ -200,10 +237,15 @@ cudaError_t union_edges(int32_t *d_edges, uint64_t m_total, const uint64_t *d_go
 }
 
 cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t nL, uint32_t flags,
-                      Csr &g, uint32_t *err_word, Alloc &al) {
+                      Csr &g, uint32_t *err_word, Alloc &al, const GraphSplit *split) {
     const uint32_t n = nU + nL;
     g.n = n;
     g.m = m;
+    g.cnt_n = n;
+    // graph-by-graph ranking when graph and degree fit one 32-bit key
+    const int dbits = split ? bits_for(split->max_n) : 0;
+    const int gbits = split ? bits_for(split->ng > 0 ? split->ng - 1 : 0) : 0;
+    const bool by_graph = split && split->ng > 1 && dbits + gbits <= 32 && dbits < 32;
     uint32_t *deg = al.get<uint32_t>(n);
     uint32_t *order = al.get<uint32_t>(n);
     uint32_t *tk = al.get<uint32_t>(n);
@@ -218,8 +260,23 @@ cudaError_t build_csr(const int32_t *d_edges, uint64_t m, uint32_t nU, uint32_t 
     al.launches++;
     k_iota<<<grid_for(n, 256), 256, 0, al.stream>>>(order, n);
     al.launches++;
-    // degrees are <= max(nU, nL); a stable sort on degree keeps ties in id order
-    BT_CUDA(radix_sort_u32(deg, order, tk, tv, n, bits_for(nU > nL ? nU : nL), al));
+    if (by_graph) {
+        uint32_t *gkey = al.get<uint32_t>(n);
+        g.vbase = al.get<uint32_t>(n);
+        if (al.err != cudaSuccess) return al.err;
+        k_graph_keys<<<grid_for(n, 256), 256, 0, al.stream>>>(deg, n, nU, nL, flags, split->ng, split->offU,
+                                                              split->offL, dbits, gkey);
+        al.launches++;
+        BT_CUDA(radix_sort_u32(gkey, order, tk, tv, n, dbits + gbits, al));
+        k_graph_rank<<<grid_for(n, 256), 256, 0, al.stream>>>(gkey, n, dbits, split->offU, split->offL, deg,
+                                                              g.vbase);
+        al.launches++;
+        al.put(gkey);
+        g.cnt_n = split->max_n;
+    } else {
+        // degrees are <= max(nU, nL); a stable sort on degree keeps ties in id order
+        BT_CUDA(radix_sort_u32(deg, order, tk, tv, n, bits_for(nU > nL ? nU : nL), al));
+    }
     // deg now holds the degrees in rank order
     BT_CUDA(cudaMemsetAsync(degr, 0, sizeof(uint64_t) * ((size_t)n + 1), al.stream));
     k_rank<<<grid_for(n, 256), 256, 0, al.stream>>>(order, deg, n, rank, degr);
@@ -299,6 +356,7 @@ cudaError_t scatter_u8(const uint8_t *in, const uint32_t *newid, uint8_t *out, u
 // Frees the CSR (and newid unless a caller took it over).
 void free_csr(Csr &g, Alloc &al) {
     al.put(g.newid);
+    al.put(g.vbase);
     al.put(g.off);
     al.put(g.adj);
     al.put(g.eid);

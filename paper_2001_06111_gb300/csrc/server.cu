@@ -35,7 +35,8 @@ namespace {
 struct Request {
     uint64_t id;
     bt_graph g;
-    uint64_t bytes;  // admission bound
+    uint64_t bytes;      // admission bound, without the counting kernels' per-block counters
+    uint64_t cnt_bytes;  // those counters for this graph (a batch needs them once, for its largest graph)
     int status = -1; // -1 pending
     double t_submit = 0, t_start = 0, t_done = 0;
 };
@@ -44,7 +45,13 @@ double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Upper bound on the device bytes a decomposition of g needs (host, O(m)).
+// Per-block counters of the counting kernels: two u32 arrays per resident
+// block, one entry per vertex of the largest graph of a batch; at most
+// 152 SMs x 2048 threads / 256-thread blocks resident.
+uint64_t counter_bound(const bt_graph &g) { return ((uint64_t)g.nU + g.nL) * 8ull * (152ull * 2048 / 256); }
+
+// Upper bound on the device bytes a decomposition of g needs (host, O(m)),
+// apart from the counters above.
 uint64_t footprint_bound(const bt_graph &g, uint32_t flags, bool device_ptrs) {
     const uint64_t m = g.m;
     const uint64_t n = (uint64_t)g.nU + g.nL;
@@ -95,7 +102,7 @@ struct bt_server {
         std::vector<bt_graph> graphs;
         for (;;) {
             batch.clear();
-            uint64_t bytes = 0;
+            uint64_t bytes = 0, cmax = 0;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 cv_work.wait(lk, [&] { return stop || !queue.empty(); });
@@ -103,7 +110,7 @@ struct bt_server {
                 // requests that can never fit are rejected first
                 for (auto it = queue.begin(); it != queue.end();) {
                     Request *r = *it;
-                    if (r->bytes <= cfg.memory_budget_bytes) {
+                    if (r->bytes + r->cnt_bytes <= cfg.memory_budget_bytes) {
                         ++it;
                         continue;
                     }
@@ -122,13 +129,15 @@ struct bt_server {
                 // last worker only when two or more large requests wait).
                 const auto is_large = [&](const Request *r) { return r->g.m >= cfg.large_edges; };
                 const auto fits = [&](const Request *r) {
-                    return in_flight_bytes + bytes + r->bytes <= cfg.memory_budget_bytes;
+                    return in_flight_bytes + bytes + r->bytes + std::max(cmax, r->cnt_bytes) <=
+                           cfg.memory_budget_bytes;
                 };
                 const auto take_large = [&]() {
                     for (auto it = queue.begin(); it != queue.end(); ++it)
                         if (is_large(*it)) {
                             if (!fits(*it)) return false;  // the oldest large one waits for memory
                             bytes += (*it)->bytes;
+                            cmax = std::max(cmax, (*it)->cnt_bytes);
                             batch.push_back(*it);
                             queue.erase(it);
                             return true;
@@ -147,6 +156,7 @@ struct bt_server {
                         if (cfg.max_batch_graphs && batch.size() >= cfg.max_batch_graphs) break;
                         it = queue.erase(it);
                         bytes += r->bytes;
+                        cmax = std::max(cmax, r->cnt_bytes);
                         batch.push_back(r);
                     }
                     return !batch.empty();
@@ -170,6 +180,7 @@ struct bt_server {
                     cv_work.wait_for(lk, std::chrono::milliseconds(1));
                     continue;
                 }
+                bytes += cmax;  // one set of counters for the whole batch
                 in_flight_bytes += bytes;
                 stats.peak_in_flight_bytes = std::max(stats.peak_in_flight_bytes, in_flight_bytes);
                 stats.batches++;
@@ -268,6 +279,7 @@ int bt_server_submit(bt_server *s, const bt_graph *g, uint64_t *request_id) {
     if (!r) return BT_ERR_NOMEM;
     r->g = *g;
     r->bytes = footprint_bound(*g, s->cfg.flags, false);
+    r->cnt_bytes = counter_bound(*g);
     r->t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -292,7 +304,7 @@ int bt_server_poll(bt_server *s, uint64_t request_id, int wait, bt_request_info 
     info->status = r->status == -1 ? BT_OK : r->status;
     info->queue_seconds = (r->t_start > 0 ? r->t_start : now_s()) - r->t_submit;
     info->latency_seconds = (info->done ? r->t_done : now_s()) - r->t_submit;
-    info->admitted_bytes = r->bytes;
+    info->admitted_bytes = r->bytes + r->cnt_bytes;
     if (info->done) {  // results delivered: forget the request
         s->reqs.erase(it);
         delete r;
