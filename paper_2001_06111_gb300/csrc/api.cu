@@ -26,7 +26,7 @@ struct bt_handle {
     std::string err;
     bt::Prof prof;
     bt_profile last{};
-    int count_nt = 512;   // schedule used by the next pipeline run
+    int count_nt = 1024;  // schedule used by the next pipeline run (1024: fewest per-block counter arrays)
     int peel_seg = 32;
     int peel_sms = 0;     // SMs the peel kernel spans (0: all); a server worker takes its share
     const bt::GraphSplit *split = nullptr;  // graphs of the batch union being prepared, if any

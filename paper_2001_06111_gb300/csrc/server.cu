@@ -194,7 +194,7 @@ struct bt_server {
             // the request path whenever a new batch shape appears
             bt_tune tune{};
             const bool alone_large = batch.size() == 1 && batch[0]->g.m >= cfg.large_edges;
-            tune.count_threads = alone_large ? 512 : 256;
+            tune.count_threads = alone_large ? 1024 : 256;
             tune.peel_item = 32;
             bt_batch_stats bs{};
             rc = bt_decompose_batch(h, graphs.data(), (uint32_t)graphs.size(), &tune, &bs,
