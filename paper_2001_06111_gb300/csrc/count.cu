@@ -295,7 +295,6 @@ void launch_count(bool index, unsigned blocks, const Csr &g, uint32_t *cnt, unsi
 
 cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt) {
     const bool index = o.inc_cnt != nullptr;
-    const uint32_t n = g.n;
     if (nt != 256 && nt != 1024) nt = 512;
     int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
