@@ -337,7 +337,9 @@ def run_updates(args):
 def serve_trace(srv, pool, big, rate, seconds, seed):
     """Submit a Poisson stream (rate req/s for `seconds`) to `srv`: each
     request is a big graph with probability 0.05, else a pool graph.  Returns
-    per-request latencies (s) and the span from first submit to last result."""
+    per-request latencies (s), the span from first submit to last result, the
+    completed and submitted counts, the edges submitted, and which requests
+    were large."""
     import threading
     rng = np.random.default_rng(seed)
     t_arr, t = [], 0.0
@@ -367,8 +369,8 @@ def serve_trace(srv, pool, big, rate, seconds, seed):
         lat.append(info["latency_seconds"])
         ok += info["status"] == 0
     span = time.perf_counter() - t0
-    serve_trace.last_big = np.array([g.m >= 1_000_000 for g in picks])
-    return np.array(lat), span, ok, len(t_arr), sum(g.m for g in picks)
+    isbig = np.array([g.m >= 1_000_000 for g in picks], dtype=bool)
+    return np.array(lat), span, ok, len(t_arr), sum(g.m for g in picks), isbig
 
 
 def run_serve(args):
@@ -389,9 +391,8 @@ def run_serve(args):
     with bt.Server(0) as srv:
         serve_trace(srv, pool[:32], big[:1], 50, 0.5, 99)  # warm-up
         for i, rate in enumerate(W["rates"]):
-            lat, span, ok, n, edges = serve_trace(srv, pool, big, rate, W["seconds"], 1000 + i)
+            lat, span, ok, n, edges, isbig = serve_trace(srv, pool, big, rate, W["seconds"], 1000 + i)
             st = srv.stats()
-            isbig = serve_trace.last_big
             sweep.append({"rate": rate, "requests": n, "ok": ok, "throughput_req_s": n / span,
                           "edges_per_s": edges / span, "p50_ms": float(np.percentile(lat, 50) * 1e3),
                           "p99_ms": float(np.percentile(lat, 99) * 1e3), "span_s": span,
@@ -402,8 +403,7 @@ def run_serve(args):
                           "large_requests": int(isbig.sum())})
             print(json.dumps({"serve_rate": sweep[-1]}), flush=True)
     with bt.Server(0, workers=1, max_batch_graphs=1) as plain:
-        lat, span, ok, n, edges = serve_trace(plain, pool, big, W["rates"][0], W["seconds"], 1000)
-        isbig = serve_trace.last_big
+        lat, span, ok, n, edges, isbig = serve_trace(plain, pool, big, W["rates"][0], W["seconds"], 1000)
         plain_res = {"rate": W["rates"][0], "requests": n, "ok": ok, "throughput_req_s": n / span,
                      "p50_ms": float(np.percentile(lat, 50) * 1e3),
                      "p99_ms": float(np.percentile(lat, 99) * 1e3), "span_s": span,
