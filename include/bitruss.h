@@ -195,8 +195,10 @@ int bt_profile_read(const bt_handle *h, bt_profile *out);
  * Capacity: m <= 262,144 edges and nU + nL <= 131,072 vertices; larger
  * graphs return BT_ERR_TOO_LARGE.  Runs on the current CUDA device.  The
  * array lives in every GPU that loads the library until the process exits;
- * the first call on a device looks up its address (call it once before any
- * stream capture).  All calls share the array and it keeps the last call's
+ * the first call on a device looks up its address and keeps it for the
+ * process (make that first call before any stream capture); after a
+ * cudaDeviceReset of that device the kept address is stale, so the entry
+ * point must not be used again in that process.  All calls share the array and it keeps the last call's
  * contents (the call clears what must start at zero); calls whose GPU work
  * overlaps race on it and must be ordered by the caller.
  * Errors: BT_ERR_ARG, BT_ERR_RANGE, BT_ERR_DUP, BT_ERR_TOO_LARGE, BT_ERR_CUDA

@@ -329,12 +329,22 @@ def bt_count_support_static(d_edges, nU: int, nL: int, d_support_out, flags: int
     """Allocation-free support count on device buffers (CUDA torch tensors):
     scratch comes from a fixed array inside the library, for callers that
     cannot allocate device memory.  Raises BitrussError on failure."""
-    s = None
-    if stream is not None:
-        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    import torch
+    if not (isinstance(d_edges, torch.Tensor) and d_edges.is_cuda and d_edges.dtype == torch.int32
+            and d_edges.dim() == 2 and d_edges.shape[1] == 2 and d_edges.is_contiguous()):
+        raise ValueError("d_edges must be a contiguous CUDA int32 tensor of shape (m, 2)")
     m = int(d_edges.shape[0])
-    rc = load().bt_count_support_static(d_edges.data_ptr(), m, nU, nL, d_support_out.data_ptr(),
-                                        flags, s)
+    if not (isinstance(d_support_out, torch.Tensor) and d_support_out.is_cuda
+            and d_support_out.element_size() == 8 and d_support_out.is_contiguous()
+            and d_support_out.numel() >= m and d_support_out.device == d_edges.device):
+        raise ValueError("d_support_out must be a contiguous 64-bit CUDA tensor with at least m "
+                         "entries on the device of d_edges")
+    with torch.cuda.device(d_edges.device):
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        rc = load().bt_count_support_static(d_edges.data_ptr(), m, nU, nL, d_support_out.data_ptr(),
+                                            flags, s)
     if rc != BT_OK:
         raise BitrussError(rc, "bt_count_support_static failed")
 

@@ -1098,8 +1098,18 @@ int bt_estimate_bytes(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL
     uint64_t csr = (n + 1) * 8 + 2 * m * (4 + 4 + 4) + n * 12;
     uint64_t sort_scratch = 2 * m * 24;
     // two u32 counters per vertex for every resident count block (at most
-    // 152 SMs x 2048 threads / 256-thread blocks)
-    uint64_t counters = 2ull * 4 * n * (152ull * 2048 / 256);
+    // SMs x resident threads per SM / 256-thread blocks, read from the
+    // current device; a GB300's 152 x 2048 when no device answers)
+    uint64_t resident = 152ull * 2048 / 256;
+    {
+        int dev = 0, sms = 0, tpm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&tpm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess &&
+            sms > 0 && tpm > 0)
+            resident = (uint64_t)sms * (uint64_t)tpm / 256;
+    }
+    uint64_t counters = 2ull * 4 * n * resident;
     uint64_t edges_b = m * (8 + 8 + 4 + 4 + 4 + 4 + 8 + 8 + 4);
     uint64_t index_b = W * (8 + 4 + 8 + 1) + (W / 2 + 1) * 16;
     *bytes_out = csr + std::max(sort_scratch, counters) + edges_b + index_b + (1ull << 20);

@@ -14,7 +14,11 @@
 // use the symbol itself as a device address: on the first call on each
 // device (with that device current) the address is fetched once with
 // cudaGetSymbolAddress and cached.  That first call should therefore come
-// before any stream capture.  All calls share the array and it keeps the
+// before any stream capture.  The cached address belongs to the device's
+// primary context: after a cudaDeviceReset of that device it is stale, and
+// the entry point must not be called again in that process.  Every call
+// synchronises the caller's stream twice (input validation and the end of
+// the count).  All calls share the array and it keeps the
 // contents of the last call; everything that must start at zero is cleared
 // by the call itself.  Two calls whose GPU work overlaps (different streams,
 // or different host threads) race on the array and give wrong results: the

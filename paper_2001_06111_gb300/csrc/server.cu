@@ -47,8 +47,10 @@ double now_s() {
 
 // Per-block counters of the counting kernels: two u32 arrays per resident
 // block, one entry per vertex of the largest graph of a batch; at most
-// 152 SMs x 2048 threads / 256-thread blocks resident.
-uint64_t counter_bound(const bt_graph &g) { return ((uint64_t)g.nU + g.nL) * 8ull * (152ull * 2048 / 256); }
+// (SMs x resident threads per SM) / 256-thread blocks are resident.
+uint64_t counter_bound(const bt_graph &g, uint64_t resident_blocks) {
+    return ((uint64_t)g.nU + g.nL) * 8ull * resident_blocks;
+}
 
 // Upper bound on the device bytes a decomposition of g needs (host, O(m)),
 // apart from the counters above.
@@ -92,6 +94,7 @@ struct bt_server {
     bool stop = false;
     uint64_t next_id = 1;
     uint64_t in_flight_bytes = 0;
+    uint64_t resident_blocks = 0;  // 256-thread blocks the device holds at once
     bt_server_stats stats{};
     std::vector<bt_handle *> handles;
 
@@ -100,6 +103,7 @@ struct bt_server {
         int rc = BT_OK;
         std::vector<Request *> batch;
         std::vector<bt_graph> graphs;
+        std::vector<int> status;
         for (;;) {
             batch.clear();
             uint64_t bytes = 0, cmax = 0;
@@ -199,13 +203,14 @@ struct bt_server {
             bt_batch_stats bs{};
             rc = bt_decompose_batch(h, graphs.data(), (uint32_t)graphs.size(), &tune, &bs,
                                     cfg.flags & BT_TIE_LOWER_FIRST);
+            // results are published under the lock only: a poll that sees a
+            // status may free the request at once
+            status.assign(batch.size(), rc);
             if (rc != BT_OK && graphs.size() > 1) {
                 // isolate the failing request(s): retry one by one
                 for (size_t i = 0; i < batch.size(); ++i)
-                    batch[i]->status = bt_decompose_batch(h, &graphs[i], 1, &tune, nullptr,
-                                                          cfg.flags & BT_TIE_LOWER_FIRST);
-            } else {
-                for (Request *r : batch) r->status = rc;
+                    status[i] = bt_decompose_batch(h, &graphs[i], 1, &tune, nullptr,
+                                                   cfg.flags & BT_TIE_LOWER_FIRST);
             }
             const double t1 = now_s();
             {
@@ -214,8 +219,9 @@ struct bt_server {
                 in_flight_bytes -= bytes;
                 stats.busy_seconds += t1 - t0;
                 stats.edges += bs.edges;
-                for (Request *r : batch) {
-                    r->t_done = t1;
+                for (size_t i = 0; i < batch.size(); ++i) {
+                    batch[i]->t_done = t1;
+                    batch[i]->status = status[i];
                     stats.completed++;
                 }
             }
@@ -241,6 +247,13 @@ int bt_server_create(bt_server **out, int device, const bt_server_config *cfg) {
         delete s;
         return BT_ERR_ARG;
     }
+    int sms = 0, tpm = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&tpm, cudaDevAttrMaxThreadsPerMultiProcessor, device) != cudaSuccess) {
+        delete s;
+        return BT_ERR_CUDA;
+    }
+    s->resident_blocks = (uint64_t)sms * (uint64_t)tpm / 256;
     for (uint32_t i = 0; i < s->cfg.workers; ++i) {
         bt_handle *h = nullptr;
         int rc = bt_create(&h, device, nullptr);
@@ -279,7 +292,7 @@ int bt_server_submit(bt_server *s, const bt_graph *g, uint64_t *request_id) {
     if (!r) return BT_ERR_NOMEM;
     r->g = *g;
     r->bytes = footprint_bound(*g, s->cfg.flags, false);
-    r->cnt_bytes = counter_bound(*g);
+    r->cnt_bytes = counter_bound(*g, s->resident_blocks);
     r->t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -10,6 +10,7 @@ calls that reuse the shared array.  This file is collected last on purpose.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2001_06111_gb300 import bitruss as bt
 from paper_2001_06111_gb300 import build, synth
 
@@ -29,6 +30,8 @@ def test_static_count_matches_allocating_count_on_two_calls():
             bt.bt_count_support_static(d_edges, g.nU, g.nL, d_sup)
             got = d_sup.cpu().numpy().view(np.uint64)
             np.testing.assert_array_equal(got, want)
+            # and the definition itself: the CPU oracle's direct enumeration
+            np.testing.assert_array_equal(got, oracle.support(g.edges, g.nU, g.nL))
 
 
 def test_static_count_rejects_oversize_graph():
