@@ -160,8 +160,9 @@ int bt_index_export(bt_handle *h, bt_bloom_rec *blooms_out, uint32_t *pairs_out,
  *   support_out: uint64[m] or NULL -- the initial supports.
  *   phi_out:     uint32[m].
  *   stats:       may be NULL.
- * Errors: as bt_build_index, plus BT_ERR_OVERFLOW (phi > 2^32-1) and
- * BT_ERR_NOCONVERGE (round limit, which is m + 1 rounds).
+ * Errors: as bt_build_index, plus BT_ERR_OVERFLOW (phi > 2^32-1),
+ * BT_ERR_NOCONVERGE (round limit, by default m + 1 rounds; see bt_set_limits)
+ * and BT_ERR_CUDA (also when a grid-barrier wait of the peel kernel ran out).
  */
 int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
                  uint64_t *support_out, uint32_t *phi_out, bt_peel_stats *stats, uint32_t flags);
@@ -177,6 +178,38 @@ int bt_profile_enable(bt_handle *h, int on);
  * on h (zeros for phases it did not run, and times only when profiling was
  * enabled).  Errors: BT_ERR_ARG. */
 int bt_profile_read(const bt_handle *h, bt_profile *out);
+
+/*
+ * Limits of the device peel loop and host-side fault injection, for
+ * diagnostics and for tests of the failure paths.  The paper has no
+ * counterpart (its algorithms are sequential CPU code without failure modes).
+ * Every field left 0 keeps the default; the settings apply to later calls on
+ * h until changed.  None of them faults, traps or hangs the GPU: each makes a
+ * bounded device wait give up, or a host step fail, and the call returns an
+ * error with the handle still usable.
+ *   peel_round_limit:   stop peeling after this many rounds and return
+ *                       BT_ERR_NOCONVERGE (default: m + 1 rounds, capped at
+ *                       2^30 - 4, more than any decomposition needs).
+ *   barrier_timeout_ns: longest wait of one block of the persistent peel
+ *                       kernel at a grid barrier; when it runs out the kernel
+ *                       raises its error word, every block returns, and the
+ *                       call returns BT_ERR_CUDA (default 20 s).
+ *   hold_barrier:       n > 0: block 0 of the peel kernel does not arrive at
+ *                       its n-th grid barrier (counted from 1), so that wait
+ *                       runs out in every block (use with a short
+ *                       barrier_timeout_ns).
+ *   fail_alloc_at:      n > 0: inside each call, device allocation number n
+ *                       (counted from 1) fails as if the device were out of
+ *                       memory; the call returns BT_ERR_NOMEM.
+ * limits == NULL restores every default.  Errors: BT_ERR_ARG (h NULL).
+ */
+typedef struct {
+    uint64_t peel_round_limit;
+    uint64_t barrier_timeout_ns;
+    uint64_t hold_barrier;
+    uint64_t fail_alloc_at;
+} bt_limits;
+int bt_set_limits(bt_handle *h, const bt_limits *limits);
 
 /*
  * Allocation-free variant of bt_count_support.  The paper has no counterpart:

@@ -34,7 +34,8 @@ EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_
             "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
             "bt_profile_read", "bt_count_support_static", "bt_decompose_batch",
             "bt_server_create", "bt_server_destroy", "bt_server_submit", "bt_server_poll",
-            "bt_server_stats_read", "bt_decompose_progressive", "bt_hierarchy", "bt_k_bitruss")
+            "bt_server_stats_read", "bt_decompose_progressive", "bt_hierarchy", "bt_k_bitruss",
+            "bt_set_limits")
 
 
 class BitrussError(RuntimeError):
@@ -75,6 +76,11 @@ class Graph(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_void_p), ("m", ctypes.c_uint64), ("nU", ctypes.c_uint32),
                 ("nL", ctypes.c_uint32), ("support_out", ctypes.c_void_p),
                 ("phi_out", ctypes.c_void_p)]
+
+
+class Limits(ctypes.Structure):
+    _fields_ = [("peel_round_limit", ctypes.c_uint64), ("barrier_timeout_ns", ctypes.c_uint64),
+                ("hold_barrier", ctypes.c_uint64), ("fail_alloc_at", ctypes.c_uint64)]
 
 
 class Tune(ctypes.Structure):
@@ -167,6 +173,7 @@ def load(path: str = LIB_PATH):
         lib.bt_decompose_progressive.argtypes = [P, P, U64, U32, U32, ctypes.c_double, P, P,
                                                  ctypes.POINTER(PcStats), U32]
         lib.bt_profile_enable.argtypes = [P, I]
+        lib.bt_set_limits.argtypes = [P, ctypes.POINTER(Limits)]
         lib.bt_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         lib.bt_estimate_bytes.argtypes = [P, U64, U32, U32, U32, ctypes.POINTER(U64),
                                           ctypes.POINTER(U64)]
@@ -431,6 +438,14 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def bt_set_limits(h: Handle, peel_round_limit: int = 0, barrier_timeout_ns: int = 0,
+                  hold_barrier: int = 0, fail_alloc_at: int = 0) -> None:
+    """Diagnostic limits and host-side fault injection for later calls on h
+    (all zero: the defaults).  See bt_set_limits in include/bitruss.h."""
+    lim = Limits(peel_round_limit, barrier_timeout_ns, hold_barrier, fail_alloc_at)
+    _check(h, load().bt_set_limits(h.ptr, ctypes.byref(lim)))
 
 
 def bt_profile_enable(h: Handle, on: bool = True):

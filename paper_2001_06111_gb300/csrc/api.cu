@@ -33,6 +33,7 @@ struct bt_handle {
     std::map<uint64_t, std::pair<int, int>> tuned;  // batch signature -> (count_nt, peel_seg)
     unsigned char *pinned = nullptr;  // page-locked staging for batch copies
     size_t pinned_bytes = 0;
+    bt_limits limits{};  // bt_set_limits (all zero: defaults)
 };
 
 namespace {
@@ -74,6 +75,7 @@ bt::Alloc make_alloc(bt_handle *h) {
     al.stream = h->stream;
     al.pool = h->pool;
     al.prof = &h->prof;
+    al.limits = &h->limits;
     return al;
 }
 
@@ -538,6 +540,8 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
         if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling");
         else if (pr.status == BT_ERR_OVERFLOW)
             rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
+        else if (pr.status == BT_ERR_CUDA)
+            rc = fail(h, BT_ERR_CUDA, "peeling stopped: a grid-barrier wait of the peel kernel ran out");
         else if (pr.status != BT_OK)
             rc = fail(h, pr.status, "peeling did not converge within its round limit");
     }
@@ -571,6 +575,12 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
     }
     cudaStreamSynchronize(h->stream);
     return rc;
+}
+
+int bt_set_limits(bt_handle *h, const bt_limits *limits) {
+    if (!h) return BT_ERR_ARG;
+    h->limits = limits ? *limits : bt_limits{};
+    return BT_OK;
 }
 
 int bt_profile_enable(bt_handle *h, int on) {

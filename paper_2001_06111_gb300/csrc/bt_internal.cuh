@@ -38,6 +38,10 @@ struct Alloc {
     // get() then bump-allocates inside it and put() does nothing.
     unsigned char *arena = nullptr;
     size_t arena_size = 0, arena_used = 0;
+    // Limits and host-side fault injection of the handle (bt_set_limits), or
+    // null.  fail_alloc_at = n > 0 makes allocation number n of this call fail.
+    const bt_limits *limits = nullptr;
+    uint64_t n_allocs = 0;
     void mark(int phase, bool end) {
         if (prof && prof->on) {
             cudaEventRecord(prof->ev[2 * phase + (end ? 1 : 0)], stream);
@@ -47,6 +51,10 @@ struct Alloc {
     template <typename T>
     T *get(size_t count) {
         if (err != cudaSuccess) return nullptr;
+        if (limits && limits->fail_alloc_at && ++n_allocs == limits->fail_alloc_at) {
+            err = cudaErrorMemoryAllocation;
+            return nullptr;
+        }
         void *p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
@@ -161,12 +169,13 @@ struct Index {
     uint32_t *bloom_k = nullptr;     // [nb] bloom numbers
     uint32_t *bloom_off = nullptr;   // [nb+1] first pair of each bloom
     uint2 *pairs = nullptr;          // [w2] (e_uv, e_vw) twin edge ids
-    uint32_t *pair_bloom = nullptr;  // [w2]
     uint64_t *inc_off = nullptr;     // [m+1]
-    uint32_t *inc = nullptr;         // [links] pair ids linked to each edge
+    // [links] per edge: (pair id, bloom id | side << 31), side 0 when the
+    // edge is the pair's first member (e_uv), 1 when it is the second
+    uint2 *inc = nullptr;
     uint32_t *newid = nullptr;       // [m] input edge id -> internal id (ids above are internal)
     size_t bytes() const {
-        return nb * 8 + 4 + w2 * 12 + (m + 1) * 8 + links * 4;
+        return nb * 8 + 4 + w2 * 8 + (m + 1) * 8 + links * 8;
     }
 };
 cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, Alloc &al,

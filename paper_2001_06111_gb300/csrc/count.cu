@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NT) k_emit(
     uint32_t *cnt_all, uint32_t *aux_all, const uint64_t *__restrict__ bloom_base,
     const uint64_t *__restrict__ pair_base, const uint64_t *__restrict__ inc_off,
     uint32_t *inc_fill, uint32_t *bloom_k, uint32_t *bloom_off, uint2 *pairs,
-    uint32_t *pair_bloom, uint32_t *inc, uint32_t *queue, const uint8_t *__restrict__ assigned) {
+    uint2 *inc, uint32_t *queue, const uint8_t *__restrict__ assigned) {
     __shared__ Chunk<NT> ch;
     __shared__ uint32_t s_q;
     // bloom count (high 32 bits) and pair count (low 32 bits) of the vertex,
@@ -252,14 +252,14 @@ __global__ void __launch_bounds__(NT) k_emit(
                     const bool fu = assigned && assigned[euv], fw = assigned && assigned[evw];
                     // an assigned edge is flagged in bit 31 and gets no link
                     pairs[slot] = make_uint2(euv | (fu ? 0x80000000u : 0u), evw | (fw ? 0x80000000u : 0u));
-                    pair_bloom[slot] = (uint32_t)B;
+                    // each link carries its bloom and which member of the pair the edge is
                     if (!fu) {
                         uint32_t q1 = atomicAdd(&inc_fill[euv], 1u);
-                        inc[inc_off[euv] + q1] = slot;
+                        inc[inc_off[euv] + q1] = make_uint2(slot, (uint32_t)B);
                     }
                     if (!fw) {
                         uint32_t q2 = atomicAdd(&inc_fill[evw], 1u);
-                        inc[inc_off[evw] + q2] = slot;
+                        inc[inc_off[evw] + q2] = make_uint2(slot, (uint32_t)B | 0x80000000u);
                     }
                 }
             }
@@ -346,7 +346,8 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     ix.nb = h_tot[0];
     ix.w2 = h_tot[1];
     ix.links = h_tot[2];  // 2 w2, less the links of assigned edges in a compressed index
-    if (ix.w2 >= 0xFFFFFFFFull || ix.nb >= 0xFFFFFFFFull) {
+    // pair ids are u32; bloom ids keep bit 31 free for the link's side
+    if (ix.w2 >= 0xFFFFFFFFull || ix.nb >= 0x80000000ull) {
         al.put(bloom_base);
         al.put(pair_base);
         al.put(tot);
@@ -355,8 +356,7 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     ix.bloom_k = al.get<uint32_t>(ix.nb);
     ix.bloom_off = al.get<uint32_t>(ix.nb + 1);
     ix.pairs = al.get<uint2>(ix.w2);
-    ix.pair_bloom = al.get<uint32_t>(ix.w2);
-    ix.inc = al.get<uint32_t>(ix.links);
+    ix.inc = al.get<uint2>(ix.links);
     uint32_t *inc_fill = al.get<uint32_t>(m);
     int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
@@ -374,7 +374,7 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     al.mark(kPhEmit, false);
 #define BT_EMIT_ARGS                                                                         \
     g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, g.vbase, g.cnt_n, cnt, aux, bloom_base, pair_base, ix.inc_off,  \
-        inc_fill, ix.bloom_k, ix.bloom_off, ix.pairs, ix.pair_bloom, ix.inc, queue, c.assigned
+        inc_fill, ix.bloom_k, ix.bloom_off, ix.pairs, ix.inc, queue, c.assigned
     if (nt == 256) k_emit<256><<<blocks, 256, 0, al.stream>>>(BT_EMIT_ARGS);
     else if (nt == 1024) k_emit<1024><<<blocks, 1024, 0, al.stream>>>(BT_EMIT_ARGS);
     else k_emit<512><<<blocks, 512, 0, al.stream>>>(BT_EMIT_ARGS);
@@ -399,7 +399,6 @@ void free_index(Index &ix, Alloc &al) {
     al.put(ix.bloom_k);
     al.put(ix.bloom_off);
     al.put(ix.pairs);
-    al.put(ix.pair_bloom);
     al.put(ix.inc_off);
     al.put(ix.inc);
     ix = Index{};

@@ -37,7 +37,10 @@
 // the new value yet.  Work is split into items of at most kSeg entries, so no
 // warp straggles on a hub edge or bloom.  A twin pair carries the round it
 // died in; the edges of a batch race to stamp it with atomicCAS, so exactly
-// one of them counts it in C(B).  Counters and work lists rotate by round
+// one of them counts it in C(B); the stamp also records which members of the
+// pair are in the batch (the killer's side bit, and the other member's bit
+// when it stamps the same round), so the bloom phase knows which member
+// loses k_B - 1 without reading edge states.  Counters and work lists rotate by round
 // (C by 3, bloom items by 4, batch sizes by 3, incidence items by 2) so each
 // is reset a barrier after its last reader.  Data written by other blocks
 // during the kernel is read with L2 (.cg) loads.
@@ -61,7 +64,10 @@ constexpr uint32_t kSmall = 2;
 // links per thread, for the edges whose links fit in the first kBlockLinks
 constexpr uint32_t kJoinCap = kPeelThreads;
 constexpr uint32_t kBlockLinks = 2 * kPeelThreads;
-constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s
+constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s (default)
+// pair death stamps: round << 2 | (first member in the batch) | (second << 1);
+// kAlive (all ones) is never a stamp while rounds stay below kMaxRounds
+constexpr uint32_t kMaxRounds = (1u << 30) - 4u;
 constexpr uint32_t kErrBarrier = 1u;
 constexpr uint32_t kErrRounds = 2u;
 constexpr uint32_t kErrPeelOverflow = 4u;
@@ -93,14 +99,13 @@ struct Ctl {
 struct PeelArgs {
     uint64_t m;
     const uint64_t *inc_off;
-    const uint32_t *inc;
+    const uint2 *inc;  // (pair, bloom | side << 31)
     const uint2 *pairs;
-    const uint32_t *pair_bloom;
     const uint32_t *bloom_off;
     long long *sup;
     uint32_t *state;
     uint32_t *phi;
-    uint32_t *died;           // round a twin pair died in (kAlive while alive)
+    uint32_t *died;           // death stamp of a twin pair (kAlive while alive)
     unsigned long long *bw;   // per bloom: last round that touched it << 32 | k_B after it
     uint32_t *Cb[3];          // C_r by round mod 3
     uint4 *items[2];          // (edge, first link lo, first link hi, count | head flag << 31)
@@ -111,6 +116,8 @@ struct PeelArgs {
     uint64_t bseg_cap;
     Ctl *ctl;
     uint64_t round_limit;
+    unsigned long long barrier_timeout_ns;
+    unsigned long long hold_barrier;  // 0, or n: block 0 skips its arrival at barrier n (from 1)
     // progressive compression: peel only the m_active unassigned edges, start
     // at level k_init, and record phi only for levels >= assign_from
     uint64_t m_active;
@@ -161,14 +168,17 @@ struct SnapVals {
     unsigned long long w;
 };
 
-__device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no, const Snap &sn, SnapVals *s_v) {
+__device__ bool grid_barrier(const PeelArgs &a, unsigned long long &bar_no, const Snap &sn, SnapVals *s_v) {
+    Ctl *ctl = a.ctl;
     __syncthreads();
     __shared__ int s_ok;
     const unsigned long long target = (bar_no + 1) * gridDim.x;
     ++bar_no;
     if (threadIdx.x == 0) {
         int ok = 1;
-        arrive_release(&ctl->bar_count);
+        // a held barrier (fault injection) never completes: every block's
+        // wait below runs out and raises the error word
+        if (!(blockIdx.x == 0 && bar_no == a.hold_barrier)) arrive_release(&ctl->bar_count);
         if (load_acquire(&ctl->bar_count) < target) {
             const unsigned long long t0 = now_ns();
             unsigned int spins = 0;
@@ -178,7 +188,7 @@ __device__ bool grid_barrier(Ctl *ctl, unsigned long long &bar_no, const Snap &s
                         ok = 0;
                         break;
                     }
-                    if (now_ns() - t0 > kBarrierTimeoutNs) {
+                    if (now_ns() - t0 > a.barrier_timeout_ns) {
                         atomicOr(&ctl->err, kErrBarrier);
                         ok = 0;
                         break;
@@ -262,6 +272,17 @@ __device__ __forceinline__ bool count_kill(const PeelArgs &a, uint32_t B, uint32
     return atomicAdd(&a.Cb[q % 3u][B], 1u) == 0u;
 }
 
+// An edge of the batch of round q kills pair p, of which it is member `side`
+// (0 first, 1 second).  The first edge to stamp the pair counts it (true);
+// a twin of the same batch adds its side bit to the stamp.
+__device__ __forceinline__ bool kill_pair(const PeelArgs &a, uint32_t p, uint32_t side, uint32_t q) {
+    const uint32_t bit = 1u << side;
+    const uint32_t old = atomicCAS(&a.died[p], kAlive, (q << 2) | bit);
+    if (old == kAlive) return true;
+    if ((old >> 2) == q) atomicOr(&a.died[p], bit);
+    return false;
+}
+
 // Whole warp (converged): each lane's pairs killed for round q (won[r], bloom
 // B[r]) are counted, and the blooms killed for the first time in round q get
 // their bloom items (one per kSeg pairs, each with k_B at the start of round
@@ -320,21 +341,22 @@ __device__ __forceinline__ void apply_slot(const PeelArgs &a, uint32_t d, uint2 
     const bool fx = pr.x >> 31, fy = pr.y >> 31;
     const uint32_t ex = pr.x & 0x7FFFFFFFu, ey = pr.y & 0x7FFFFFFFu;
     const uint32_t q = round + 1u;
-    if (d == kAlive || d == q) {
+    const uint32_t dr = d >> 2;  // round of death (kAlive: 0x3FFFFFFF, no round)
+    if (d == kAlive || dr == q) {
         // alive during this round (a pair killed for the next round still is):
         // one butterfly lost per dead pair
         if (!fx && decrement(a, ex, c, L)) join_next<kSeg>(a, ex, q, L.k, s_je, s_jn);
         if (!fy && decrement(a, ey, c, L)) join_next<kSeg>(a, ey, q, L.k, s_je, s_jn);
         upd += (fx ? 0 : 1) + (fy ? 0 : 1);
-    } else if (d == round && kB > 1u) {
-        // died now: a member outside S loses its k_B - 1 butterflies
-        const uint32_t sx = fx ? round : __ldcg(&a.state[ex]);
-        const uint32_t sy = fy ? round : __ldcg(&a.state[ey]);
-        if (sx != round) {
+    } else if (dr == round && kB > 1u) {
+        // died now: a member outside S (its bit not stamped) loses its
+        // k_B - 1 butterflies
+        const bool sx = fx || (d & 1u), sy = fy || (d & 2u);
+        if (!sx) {
             if (decrement(a, ex, (long long)kB - 1, L)) join_next<kSeg>(a, ex, q, L.k, s_je, s_jn);
             ++upd;
         }
-        if (sy != round) {
+        if (!sy) {
             if (decrement(a, ey, (long long)kB - 1, L)) join_next<kSeg>(a, ey, q, L.k, s_je, s_jn);
             ++upd;
         }
@@ -412,7 +434,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             }
             {
                 const Snap sn{{nullptr, nullptr, nullptr, nullptr, &ctl->n_near[L.nq ^ 1u]}, &ctl->minsup};
-                if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+                if (!grid_barrier(a, bar_no, sn, &s_v)) break;
             }
             unsigned long long mn = s_v.w;
             v_near = s_v.u[4];
@@ -450,7 +472,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 if (lane == 0 && best != ~0ull) atomicMin(&ctl->minsup2, best);
                 {
                     const Snap sn{{nullptr, nullptr, nullptr, nullptr, &ctl->n_alive[ap ^ 1u]}, &ctl->minsup2};
-                    if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+                    if (!grid_barrier(a, bar_no, sn, &s_v)) break;
                 }
                 mn = s_v.w;
                 if (mn == ~0ull) break;  // no alive edge: cannot happen while remaining > 0
@@ -479,7 +501,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 if (gtid == 0) atomicAdd(&ctl->windows, 1ull);
                 {
                     const Snap sn{{nullptr, nullptr, nullptr, nullptr, &ctl->n_near[L.nq]}, nullptr};
-                    if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+                    if (!grid_barrier(a, bar_no, sn, &s_v)) break;
                 }
                 v_near = s_v.u[4];
                 if (gtid == 0) ctl->minsup2 = ~0ull;
@@ -542,7 +564,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 const Snap sn{{&ctl->n_edges[c3], &ctl->n_items[par], &ctl->n_bseg[b4], &ctl->n_bseg[bp],
                                &ctl->n_near[L.nq]},
                               nullptr};
-                if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+                if (!grid_barrier(a, bar_no, sn, &s_v)) break;
             }
             n_batch = s_v.u[0];
             n_items = s_v.u[1];
@@ -568,21 +590,19 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     // a small item is this lane's own: its links' loads and
                     // stamps go out together
                     const uint64_t j0 = (uint64_t)it.z << 32 | it.y;
-                    uint32_t p[kSmall], B[kSmall];
+                    uint2 l[kSmall];
+                    uint32_t B[kSmall];
                     bool won[kSmall];
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r) {
                         won[r] = cnt <= kSmall && r < cnt;
-                        p[r] = won[r] ? a.inc[j0 + r] : 0u;
-                        B[r] = 0;
+                        l[r] = won[r] ? a.inc[j0 + r] : make_uint2(0u, 0u);
+                        B[r] = l[r].y & 0x7FFFFFFFu;
                     }
-#pragma unroll
-                    for (uint32_t r = 0; r < kSmall; ++r)
-                        if (won[r]) B[r] = a.pair_bloom[p[r]];
                     // the first edge of the batch to stamp a pair kills it (once)
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r)
-                        if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
+                        if (won[r]) won[r] = kill_pair(a, l[r].x, l[r].y >> 31, round);
                     warp_kills<kSeg, kSmall>(a, round, B, won, lane);
                 }
                 // items with many links: the whole warp, one item at a time
@@ -594,26 +614,24 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     const uint32_t jlo = __shfl_sync(kFull, it.y, src);
                     const uint32_t jhi = __shfl_sync(kFull, it.z, src);
                     const uint64_t j0 = ((uint64_t)jhi << 32 | jlo) + lane;
-                    uint32_t p[R], B[R];
+                    uint2 l[R];
+                    uint32_t B[R];
                     bool won[R];
 #pragma unroll
                     for (uint32_t r = 0; r < R; ++r) {
                         won[r] = lane + 32u * r < bcnt;
-                        p[r] = won[r] ? a.inc[j0 + 32u * r] : 0u;
-                        B[r] = 0;
+                        l[r] = won[r] ? a.inc[j0 + 32u * r] : make_uint2(0u, 0u);
+                        B[r] = l[r].y & 0x7FFFFFFFu;
                     }
 #pragma unroll
                     for (uint32_t r = 0; r < R; ++r)
-                        if (won[r]) B[r] = a.pair_bloom[p[r]];
-#pragma unroll
-                    for (uint32_t r = 0; r < R; ++r)
-                        if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, round) == kAlive;
+                        if (won[r]) won[r] = kill_pair(a, l[r].x, l[r].y >> 31, round);
                     warp_kills<kSeg, R>(a, round, B, won, lane);
                 }
             }
             {
                 const Snap sn{{nullptr, nullptr, &ctl->n_bseg[b4], nullptr, nullptr}, nullptr};
-                if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+                if (!grid_barrier(a, bar_no, sn, &s_v)) break;
             }
             nb_cur = s_v.u[2];
         }
@@ -637,7 +655,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 #pragma unroll
                     for (uint32_t r = 0; r < kSmall; ++r) {
                         const bool act = r < cnt;
-                        d[r] = act ? __ldcg(&a.died[it.y + r]) : round + 2u;  // inactive: no case applies
+                        d[r] = act ? __ldcg(&a.died[it.y + r]) : (round + 2u) << 2;  // inactive: no case applies
                         pr[r] = act ? a.pairs[it.y + r] : make_uint2(0, 0);
                     }
 #pragma unroll
@@ -657,7 +675,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 #pragma unroll
                     for (uint32_t r = 0; r < R; ++r) {
                         const bool act = lane + 32u * r < bcnt;
-                        d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : round + 2u;
+                        d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : (round + 2u) << 2;
                         pr[r] = act ? a.pairs[p0 + 32u * r] : make_uint2(0, 0);
                     }
 #pragma unroll
@@ -698,29 +716,27 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 if (threadIdx.x == 0) atomicAdd(&ctl->n_edges[q % 3u], nj);
                 __syncthreads();
                 const uint32_t lim = total < kBlockLinks ? total : kBlockLinks;
-                uint32_t p[2], B[2];
+                uint2 l[2];
+                uint32_t B[2];
                 bool won[2];
 #pragma unroll
                 for (uint32_t r = 0; r < 2; ++r) {
                     const uint32_t x = threadIdx.x + r * (uint32_t)kPeelThreads;
                     won[r] = false;
-                    p[r] = 0;
-                    B[r] = 0;
+                    l[r] = make_uint2(0u, 0u);
                     if (x < lim) {
                         const uint32_t j = dev::last_le_u32(s_joff, nj, x);
                         if (s_joff[j] + s_jd[j] <= kBlockLinks) {
                             won[r] = true;
-                            p[r] = a.inc[s_jib[j] + (x - s_joff[j])];
+                            l[r] = a.inc[s_jib[j] + (x - s_joff[j])];
                         }
                     }
+                    B[r] = l[r].y & 0x7FFFFFFFu;
                 }
-#pragma unroll
-                for (uint32_t r = 0; r < 2; ++r)
-                    if (won[r]) B[r] = a.pair_bloom[p[r]];
                 // the first edge of the batch to stamp a pair kills it (once)
 #pragma unroll
                 for (uint32_t r = 0; r < 2; ++r)
-                    if (won[r]) won[r] = atomicCAS(&a.died[p[r]], kAlive, q) == kAlive;
+                    if (won[r]) won[r] = kill_pair(a, l[r].x, l[r].y >> 31, q);
                 warp_kills<kSeg, 2>(a, q, B, won, lane);
                 if (threadIdx.x == 0) s_jn = 0;
             }
@@ -732,7 +748,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             const Snap sn{{&ctl->n_edges[q % 3u], &ctl->n_items[q & 1u], &ctl->n_bseg[q & 3u], &ctl->n_bseg[b4],
                            &ctl->n_near[L.nq]},
                           nullptr};
-            if (!grid_barrier(ctl, bar_no, sn, &s_v)) break;
+            if (!grid_barrier(a, bar_no, sn, &s_v)) break;
         }
         remaining -= n_batch;
         ++round;
@@ -795,7 +811,6 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     a.inc_off = ix.inc_off;
     a.inc = ix.inc;
     a.pairs = ix.pairs;
-    a.pair_bloom = ix.pair_bloom;
     a.bloom_off = ix.bloom_off;
     a.phi = phi_out;
     a.sup = al.get<long long>(m);
@@ -812,7 +827,14 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     a.item_cap = item_cap;
     a.bseg_cap = bseg_cap;
     a.ctl = al.get<Ctl>(1);
-    a.round_limit = m + 1;
+    {
+        const bt_limits *lim = al.limits;
+        uint64_t rl = m + 1 < kMaxRounds ? m + 1 : kMaxRounds;
+        if (lim && lim->peel_round_limit && lim->peel_round_limit < rl) rl = lim->peel_round_limit;
+        a.round_limit = rl;
+        a.barrier_timeout_ns = (lim && lim->barrier_timeout_ns) ? lim->barrier_timeout_ns : kBarrierTimeoutNs;
+        a.hold_barrier = lim ? lim->hold_barrier : 0;
+    }
     a.m_active = (opts && opts->assigned) ? opts->m_active : m;
     a.k_init = opts ? opts->k_init : 0;
     a.assign_from = opts ? opts->assign_from : 0;

@@ -11,6 +11,7 @@ import oracle
 from paper_2001_06111_gb300 import bitruss as bt
 from paper_2001_06111_gb300 import build, synth
 from tests import pins
+from tests.digests import assert_matches_digest, oracle_digest
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -53,6 +54,13 @@ def test_paper_example(h):
     # (Section V-B) e6..e8 at k=1 and the six blue edges (three twin pairs of
     # B0) at k=2 -> three levels of one round each
     assert st["rounds"] == 3 and st["levels"] == 3 and st["phi_max"] == 2
+    # support updates of the BU++ example under the Fig. 6 index (the last
+    # flags above): the round at MBS = 1 kills the pairs (e5, e6) and (e7, e8)
+    # of B1; e5 is outside the batch and loses k_B - 1 = 1 butterfly, the
+    # twins e7, e8 are both in it, and B1 keeps no live pair.  The round at
+    # MBS = 2 takes all three twin pairs of B0 with both members in the
+    # batch, so no support changes: exactly one update in all.
+    assert st["support_updates"] == 1
 
 
 def test_paper_example_index_fig6(h):
@@ -209,11 +217,19 @@ def test_device_pointer_path(h):
     np.testing.assert_array_equal(phi_d.cpu().numpy().view(np.uint32), phi_h)
 
 
-def test_medium_workload_full_size(h):
+def test_medium_workload_full_size_exact(h):
     """The 2M-edge workload at full size, in the configuration the benchmark
-    times: supports of sampled edges recomputed one by one by the oracle,
-    bitruss numbers checked by the local fixpoint property on sampled edges,
-    and global invariants on all edges."""
+    times: every support and bitruss number equals the CPU oracle's (digests
+    of the oracle's full arrays, computed offline)."""
+    g = synth.medium()
+    sup, phi, st = decompose(h, g.edges, g.nU, g.nL)
+    assert_matches_digest(g, sup, phi, oracle_digest("medium"))
+
+
+def test_medium_workload_full_size(h):
+    """The 2M-edge workload at full size: supports of sampled edges
+    recomputed one by one by the oracle, bitruss numbers checked by the local
+    fixpoint property on sampled edges, and global invariants on all edges."""
     g = synth.medium()
     sup, phi, st = decompose(h, g.edges, g.nU, g.nL)
     rng = np.random.default_rng(12)

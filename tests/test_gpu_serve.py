@@ -1,9 +1,14 @@
 """Serving with continuous batching (bt_server_*): requests that arrive while
-the GPU is busy are batched together, and every result equals the graph's
-decomposition alone."""
+the GPU is busy are batched together, every result equals the graph's
+decomposition alone, and results of requests small enough for the CPU oracle
+(<= 20,000 edges) equal the oracle's exactly."""
+import threading
+import time
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_2001_06111_gb300 import bitruss as bt
 from paper_2001_06111_gb300 import build, synth
 
@@ -33,6 +38,10 @@ def test_requests_batched_while_busy_and_exact(alone):
         s1, p1 = alone(g.edges, g.nU, g.nL)
         np.testing.assert_array_equal(sup, s1)
         np.testing.assert_array_equal(phi, p1)
+        if g.m <= 20000:
+            sr, pr = oracle.bitruss(g.edges, g.nU, g.nL)
+            np.testing.assert_array_equal(sup, sr)
+            np.testing.assert_array_equal(phi.astype(np.uint64), pr)
 
 
 def test_concurrent_workers_exact(alone):
@@ -70,3 +79,36 @@ def test_large_requests_alone_small_ones_pass(alone):
     for (info, (_, phi)), g in zip(res, large + small):
         assert info["status"] == bt.BT_OK
         np.testing.assert_array_equal(phi, alone(g.edges, g.nU, g.nL)[1])
+
+
+def test_nonblocking_polls_while_batches_complete():
+    """Polls with wait=0 in tight loops from several threads while workers
+    finish batches: a request is reported (and released) only once its result
+    and completion time are both published, and every result matches the
+    oracle."""
+    build.build()
+    gs = [synth.batch_graph(300 + i, hi=8000) for i in range(48)]
+    ref = [oracle.bitruss(g.edges, g.nU, g.nL) for g in gs]
+    out = [None] * len(gs)
+    with bt.Server(0, workers=2) as srv:
+        ids = [srv.submit(g.edges, g.nU, g.nL, want_support=True) for g in gs]
+
+        def poller(part):
+            for i in part:
+                t_end = time.time() + 120
+                while True:
+                    info, res = srv.poll(ids[i], wait=False)
+                    if info["done"]:
+                        out[i] = (info, res)
+                        break
+                    assert time.time() < t_end
+        th = [threading.Thread(target=poller, args=(range(t, len(gs), 4),)) for t in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+    for (info, (sup, phi)), (sr, pr) in zip(out, ref):
+        assert info["status"] == bt.BT_OK
+        assert info["latency_seconds"] >= info["queue_seconds"] >= 0
+        np.testing.assert_array_equal(sup, sr)
+        np.testing.assert_array_equal(phi.astype(np.uint64), pr)
