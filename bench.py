@@ -1,11 +1,16 @@
-"""Benchmark: single-graph bitruss decomposition on the 2M-edge skewed workload.
+"""Benchmark: single-graph bitruss decomposition on the 30M-edge planted workload.
 
 A step is one full pass of the path -- rank-ordered CSR build, wedge count
 with support attribution, BE-Index emit and batch peeling -- over one
-synthetic graph (|U|=200,000, |L|=80,000, m=2,000,000, exponents 2.1/2.4,
-degree cap 20,000).  The timed value uses device-resident edges and outputs;
-``e2e`` repeats the step through the C ABI with host buffers (host->device
-edge copy and device->host support/phi copy inside the timed region).
+synthetic graph: Chung-Lu |U|=2,000,000, |L|=500,000, 30,000,000 distinct
+edges, exponents 2.0/2.3, with 200 planted dense bicliques (sides uniform in
+[50, 300], density 0.9) placed first -- the largest single-graph workload,
+with deep peeling levels and large blooms.  The timed value uses
+device-resident edges and outputs; ``e2e`` repeats the step through the C
+ABI with host buffers (host->device edge copy and device->host support/phi
+copy inside the timed region).  At one GPU the same JSON line also carries
+the 2M-edge workload (``medium_2M``) and the 4,096-graph batch
+(``batch_4096``: one batched call against one call per graph).
 
 Multi-GPU: one process per GPU (torchrun); each rank decomposes its own
 replica, no collective on the data path (replicas only, weak scaling).
@@ -30,22 +35,36 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
+    "large": dict(name="chunglu-2M-500k-30M-planted200", nU=2000000, nL=500000, m=30000000, gammaU=2.0,
+                  gammaL=2.3, cap=0, seed=3, nplant=200, plant_lo=50, plant_hi=300, plant_p=0.9),
     "medium": dict(name="chunglu-200k-80k-2M-cap20k", nU=200000, nL=80000, m=2000000, gammaU=2.1,
                    gammaL=2.4, cap=20000, seed=2),
     "small": dict(name="chunglu-2k-1.5k-20k", nU=2000, nL=1500, m=20000, gammaU=2.2, gammaL=2.5,
                   cap=0, seed=1),
     "batch": dict(name="batch-4096-chunglu-logU(100,200000)", graphs=4096),
     "serve": dict(name="poisson-serve-batchdist+5%-2M", pool=256, big=4,
-                  rates=[50, 100, 200, 500, 1000, 2000], seconds=4.0),
+                  rates=[50, 100, 200, 500, 1000, 2000], seconds=60.0),
     # support updates and index sizes, BiT-BU++ against BiT-PC (Figs. 10-11)
     "updates": dict(name="updates-and-index-size", configs={"small": (0.02, 0.1), "medium": (0.02, 0.1),
                                                            "large": (0.05,)}),
 }
-WORKLOAD = WORKLOADS["medium"]
+WORKLOAD = WORKLOADS["large"]
+WL_KEY = "large"
 METRIC = "edges decomposed/s"
 UNIT = "edges/s"
-CPU_SAMPLE_FRAC = 0.3   # vertex-induced sample for the oracle baseline
-REF_SAMPLE_FRAC = 0.2   # per-step sample for the reference arm
+# vertex-induced samples (the sampling of Section VI's scalability study) the
+# CPU oracle decomposes: the baseline leg (one sample) and the reference arm
+# (one sample per step), sized to a few to tens of seconds of oracle time
+CPU_SAMPLE_FRAC = {"large": 0.07, "medium": 0.3, "small": 1.0}
+REF_SAMPLE_FRAC = {"large": 0.05, "medium": 0.2, "small": 1.0}
+
+
+def gen_workload(w):
+    """The seeded synthetic graph of single-graph workload w."""
+    from paper_2001_06111_gb300 import synth
+    return synth.chunglu(w["nU"], w["nL"], w["m"], w["gammaU"], w["gammaL"], seed=w["seed"], cap=w["cap"],
+                         nplant=w.get("nplant", 0), plant_lo=w.get("plant_lo", 0),
+                         plant_hi=w.get("plant_hi", 0), plant_p=w.get("plant_p", 0.0), name=w["name"])
 
 
 def load_peaks():
@@ -137,21 +156,32 @@ def dist_env():
 
 
 def algorithmic_bytes(p):
-    """Per-launch algorithmic bytes of the count, emit and peel kernels
-    (W wedges, W2 bloom wedges, NB blooms, m edges; the peel's link visits,
-    pair-slot visits and support updates are counted by the library)."""
+    """Per-launch algorithmic bytes of the count, emit and peel kernels (W
+    priority-obeyed wedges, W2 bloom wedges, NB blooms, m edges):
+      count (passes A and B)  4W + 12m  +  8W + 8 W2 + 8m
+      emit                    8W + 8 W2 (twin pairs) + 8 W2 (links) + 12 NB
+      peel                    9 per edge-list entry a level jump scans
+                              + 8 per link visit + 10 per bloom pair slot
+                              (two 4-byte ids and two alive bytes)
+                              + 8 per support update
+    The peel's scans, link visits, pair slots and updates are counted by the
+    library itself."""
     W, W2, NB, m = p["n_wedges"], p["n_bloom_wedges"], p["n_blooms"], p["n_edges"]
     count = 12 * W + 8 * W2 + 20 * m
-    emit = 8 * W + 20 * W2 + 12 * NB
-    peel = 25 * p["link_visits"] + 9 * p["pair_slots"] + 16 * p["support_updates"]
+    emit = 8 * W + 16 * W2 + 12 * NB
+    peel = 9 * p["scanned"] + 8 * p["link_visits"] + 10 * p["pair_slots"] + 8 * p["support_updates"]
     return {"count": count, "emit": emit, "peel": peel}
 
 
-def measured_traffic(kernel: str, workload: str):
+def measured_traffic(kernel: str, workload: str, alg_bytes=None):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or
     None when there is none or a source it lists (the kernel's own file, and
     the CSR build that numbers the edges the kernel walks) changed since the
-    capture."""
+    capture.  A summary of a smaller case of the same shape (captured where
+    the full workload is too large for a multi-pass ncu capture) lists its
+    own algorithmic bytes; its traffic is then scaled to this launch by the
+    ratio of algorithmic bytes (traffic taken to grow in proportion to the
+    work)."""
     import hashlib
     import re
     src = {"peel": "peel.cu", "count": "count.cu", "emit": "count.cu"}.get(kernel)
@@ -167,10 +197,15 @@ def measured_traffic(kernel: str, workload: str):
         with open(os.path.join(ROOT, "paper_2001_06111_gb300", "csrc", name), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != digest:
                 return None
+    m_a = re.search(r"algorithmic_bytes_per_launch \| (\d+)", text)
+    if "scaled to the full workload" in text:
+        if not m_a or not alg_bytes:
+            return None
+        return int(int(m_t.group(1)) * alg_bytes / int(m_a.group(1)))
     return int(m_t.group(1))
 
 
-WORKLOAD_PROFILE_TAG = {"medium": "chunglu-2M", "small": "chunglu-20k"}
+WORKLOAD_PROFILE_TAG = {"large": "c3shape-3M", "medium": "chunglu-2M", "small": "chunglu-20k"}
 
 
 def run_reference(args):
@@ -180,9 +215,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    g = synth.chunglu(WORKLOAD["nU"], WORKLOAD["nL"], WORKLOAD["m"], WORKLOAD["gammaU"],
-                      WORKLOAD["gammaL"], seed=WORKLOAD["seed"], cap=WORKLOAD["cap"])
-    sample = synth.vertex_sample(g, REF_SAMPLE_FRAC, 7)
+    frac = REF_SAMPLE_FRAC[WL_KEY]
+    sample = synth.vertex_sample(gen_workload(WORKLOAD), frac, 7)
     for _ in range(args.warmup):
         oracle.bitruss(sample.edges, sample.nU, sample.nL)
     t0 = time.perf_counter()
@@ -190,7 +224,7 @@ def run_reference(args):
         oracle.bitruss(sample.edges, sample.nU, sample.nL)
     dt = time.perf_counter() - t0
     value = sample.m * args.steps / dt
-    desc = (f"{int(REF_SAMPLE_FRAC * 100)}% vertex-induced sample of {WORKLOAD['name']} "
+    desc = (f"{frac * 100:g}% vertex-induced sample of {WORKLOAD['name']} "
             f"({sample.m} edges) per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -210,14 +244,13 @@ def cpu_baseline():
     import oracle
     from paper_2001_06111_gb300 import synth
 
-    g = synth.chunglu(WORKLOAD["nU"], WORKLOAD["nL"], WORKLOAD["m"], WORKLOAD["gammaU"],
-                      WORKLOAD["gammaL"], seed=WORKLOAD["seed"], cap=WORKLOAD["cap"])
-    s = synth.vertex_sample(g, CPU_SAMPLE_FRAC, 7)
+    frac = CPU_SAMPLE_FRAC[WL_KEY]
+    s = synth.vertex_sample(gen_workload(WORKLOAD), frac, 7)
     t0 = time.perf_counter()
     oracle.bitruss(s.edges, s.nU, s.nL)
     dt = time.perf_counter() - t0
     return {"value": s.m / dt, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-            "sample": (f"{int(CPU_SAMPLE_FRAC * 100)}% vertex-induced sample of {WORKLOAD['name']}"
+            "sample": (f"{frac * 100:g}% vertex-induced sample of {WORKLOAD['name']}"
                        f" ({s.m} edges), support count on all cores, peeling single-threaded"),
             "seconds": dt}
 
@@ -420,22 +453,134 @@ def run_serve(args):
     return 0
 
 
+def time_steps(bt, h, stream, d_edges, g, d_sup, d_phi, flush, steps, warmup):
+    """Warm-up steps, then `steps` timed steps with CUDA events on the
+    library's stream (L2 flushed before each, outside the events); returns
+    the per-step milliseconds and the library's profile of each step."""
+    import torch
+
+    def step():
+        bt.bt_decompose(h, d_edges, g.nU, g.nL, support_out=d_sup, phi_out=d_phi)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    step_ms, profs = [], []
+    for _ in range(steps):
+        flush.fill_(1)  # evict L2 between timed steps (outside the timed events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        profs.append(bt.bt_profile_read(h))
+    return step_ms, profs
+
+
+def kernel_summary(profs, workload_key):
+    """Per-kernel medians, algorithmic GB/s and the dominant kernel's roofline
+    against the measured copy bandwidth."""
+    med = lambda key: statistics.median(p[key] for p in profs)  # noqa: E731
+    p0 = profs[-1]
+    ab = algorithmic_bytes(p0)
+    peak, peak_kind = load_peaks()
+    kern = {"count": med("count_ms"), "emit": med("emit_ms"), "peel": med("peel_ms")}
+    dom = max(kern, key=kern.get)
+    achieved = ab[dom] / (kern[dom] / 1e3) / 1e9
+    return {
+        "wedges_per_s": p0["n_wedges"] / ((kern["count"] + kern["emit"]) / 1e3),
+        "phases_ms": {"csr": med("csr_ms"), "count": kern["count"], "emit": kern["emit"],
+                      "peel": kern["peel"], "call": med("total_ms")},
+        "work": {k: p0[k] for k in ("n_wedges", "n_bloom_wedges", "n_blooms", "rounds", "levels",
+                                    "support_updates", "pair_slots", "link_visits", "scanned")},
+        "kernels_gbs": {k: ab[k] / (kern[k] / 1e3) / 1e9 for k in kern if kern[k] > 0},
+        "roofline": {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes": ab[dom],
+                     "traffic": measured_traffic(dom, workload_key, ab[dom])},
+    }
+
+
+def extra_medium(bt, h, stream, flush):
+    """The 2M-edge workload (a few device-resident steps) for the same line."""
+    import torch
+    w = WORKLOADS["medium"]
+    g = gen_workload(w)
+    d_edges = torch.from_numpy(g.edges).cuda()
+    d_sup = torch.empty(g.m, dtype=torch.int64, device="cuda")
+    d_phi = torch.empty(g.m, dtype=torch.int32, device="cuda")
+    step_ms, profs = time_steps(bt, h, stream, d_edges, g, d_sup, d_phi, flush, 5, 3)
+    ms = statistics.median(step_ms)
+    out = {"workload": w["name"], "m": g.m, "value": g.m / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "steps": len(step_ms)}
+    out.update(kernel_summary(profs, "medium"))
+    return out
+
+
+def extra_batch(bt):
+    """The 4,096-graph batch through the C ABI with host buffers: one
+    bt_decompose_batch (autotuned; its first, tuning call is untimed) against
+    the one-call-per-graph path on every 8th graph; results compared graph by
+    graph on those graphs."""
+    import torch
+    graphs = gen_batch(4096)
+    gs = [(g.edges, g.nU, g.nL) for g in graphs]
+    h = bt.bt_create(0)
+    try:
+        for e, nU, nL in gs[:32]:
+            bt.bt_decompose(h, e, nU, nL)
+        _, st_tune = bt.bt_decompose_batch(h, gs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs, st = bt.bt_decompose_batch(h, gs)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        sub = list(range(0, len(gs), 8))
+        t0 = time.perf_counter()
+        plain = {i: bt.bt_decompose(h, *gs[i])[:2] for i in sub}
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t0
+    finally:
+        h.close()
+    exact = all(np.array_equal(outs[i][0], plain[i][0]) and np.array_equal(outs[i][1], plain[i][1])
+                for i in sub)
+    m_total = sum(g.m for g in graphs)
+    return {"workload": WORKLOADS["batch"]["name"], "graphs": len(gs), "edges": m_total,
+            "value": len(gs) / t_batch, "unit": "graphs/s", "ms_per_batch": t_batch * 1e3,
+            "plain_graphs_per_s": len(sub) / t_plain, "plain_sample": f"every 8th graph ({len(sub)})",
+            "speedup_vs_plain": (len(sub) / t_plain) and (len(gs) / t_batch) / (len(sub) / t_plain),
+            "bit_exact_vs_plain": bool(exact), "autotune": st_tune["tuned"],
+            "count_threads": st["count_threads"], "peel_item": st["peel_item"],
+            "rounds": st["rounds"], "io": "host buffers through the C ABI (staging inside the timed call)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=sorted(WORKLOADS),
-                    help="medium (default) is the benchmark workload; small is for profiling")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 2M-edge and 4,096-graph entries of the default line")
+    ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
+                    help="large (default) is the benchmark workload; medium and small are the "
+                         "other single-graph workloads; batch, serve and updates print their own lines")
     ap.add_argument("--rates", default="",
                     help="serve workload: comma-separated arrival rates (req/s) instead of the full sweep")
+    ap.add_argument("--seconds", type=float, default=0.0,
+                    help="serve workload: seconds of arrivals per rate (default 60)")
     args = ap.parse_args()
-    global WORKLOAD
+    global WORKLOAD, WL_KEY
+    WL_KEY = args.workload
     WORKLOAD = WORKLOADS[args.workload]
-    if args.workload == "serve" and args.rates:
-        WORKLOAD = dict(WORKLOAD, rates=[float(r) for r in args.rates.split(",")])
+    if args.workload == "serve":
+        if args.rates:
+            WORKLOAD = dict(WORKLOAD, rates=[float(r) for r in args.rates.split(",")])
+        if args.seconds:
+            WORKLOAD = dict(WORKLOAD, seconds=args.seconds)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -455,7 +600,7 @@ def main():
 
     import torch
     from paper_2001_06111_gb300 import bitruss as bt
-    from paper_2001_06111_gb300 import build, synth
+    from paper_2001_06111_gb300 import build
 
     torch.cuda.set_device(local)
     dist = None
@@ -463,8 +608,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     build.build()
-    g = synth.chunglu(WORKLOAD["nU"], WORKLOAD["nL"], WORKLOAD["m"], WORKLOAD["gammaU"],
-                      WORKLOAD["gammaL"], seed=WORKLOAD["seed"], cap=WORKLOAD["cap"])
+    g = gen_workload(WORKLOAD)
     m = g.m
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -475,31 +619,16 @@ def main():
     d_phi = torch.empty(m, dtype=torch.int32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
-    def step():
-        bt.bt_decompose(h, d_edges, g.nU, g.nL, support_out=d_sup, phi_out=d_phi)
-
-    for _ in range(args.warmup):
-        step()
+    bt.bt_decompose(h, d_edges, g.nU, g.nL, support_out=d_sup, phi_out=d_phi)  # module and pool
     torch.cuda.synchronize()
-
     clocks = ClockSampler(local)
     clocks.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
-    step_ms = []
-    profs = []
-    for _ in range(args.steps):
-        flush.fill_(1)  # evict L2 between timed steps (outside the timed events)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        profs.append(bt.bt_profile_read(h))
+    step_ms, profs = time_steps(bt, h, stream, d_edges, g, d_sup, d_phi, flush, args.steps,
+                                args.warmup - 1)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -508,15 +637,22 @@ def main():
     total_ms = max_over_ranks(sum(step_ms), dist)
     value = job_throughput(ws, m, args.steps, total_ms)
 
-    # end-to-end through the C ABI with host buffers
-    e2e_steps = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    # end-to-end through the C ABI with host buffers: the edge copy in and the
+    # support and phi copies out are inside each timed call; L2 flushed before
+    # each call (outside the timed interval), as for the device-resident steps
+    e2e_steps = min(2, args.steps)
+    e2e_s = 0.0
     for _ in range(e2e_steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         sup_h, phi_h, _ = bt.bt_decompose(h, g.edges, g.nU, g.nL)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, dist)
     e2e_value = job_throughput(ws, m, e2e_steps, e2e_s * 1e3)
+    e2e_exact = bool(np.array_equal(sup_h, d_sup.cpu().numpy().view(np.uint64)) and
+                     np.array_equal(phi_h, d_phi.cpu().numpy().view(np.uint32)))
 
     # the k-bitruss hierarchy of the decomposed graph (outside the step): the
     # order by phi and one H_k, device buffers, CUDA events on the stream
@@ -533,48 +669,48 @@ def main():
             e1.record(stream)
             e1.synchronize()
             hier[key].append(e0.elapsed_time(e1))
+    launches = int(sum(p["launches"] for p in profs))
+    summary = kernel_summary(profs, WL_KEY)
+    h.close()
+    del d_edges, d_sup, d_phi
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    p0 = profs[-1]
-    med = lambda key: statistics.median(p[key] for p in profs)  # noqa: E731
-    ab = algorithmic_bytes(p0)
-    peak, peak_kind = load_peaks()
-    kern = {"count": med("count_ms"), "emit": med("emit_ms"), "peel": med("peel_ms")}
-    dom = max(kern, key=kern.get)
-    achieved = ab[dom] / (kern[dom] / 1e3) / 1e9
+    extras = {}
+    if ws == 1 and not args.no_extras and WL_KEY == "large":
+        h2 = bt.bt_create(local, stream)
+        bt.bt_profile_enable(h2, True)
+        try:
+            extras["medium_2M"] = extra_medium(bt, h2, stream, flush)
+        finally:
+            h2.close()
+        extras["batch_4096"] = extra_batch(bt)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "nU": g.nU, "nL": g.nL, "m": m,
                    "exponents": [WORKLOAD["gammaU"], WORKLOAD["gammaL"]], "degree_cap": WORKLOAD["cap"],
-                   "seed": WORKLOAD["seed"], "parallelism": f"replicas x{ws}",
-                   "cache": "L2 flushed (256 MiB write) before every timed step"},
-        "wedges_per_s": p0["n_wedges"] / ((med("count_ms") + med("emit_ms")) / 1e3),
-        "phases_ms": {"csr": med("csr_ms"), "count": med("count_ms"), "emit": med("emit_ms"),
-                      "peel": med("peel_ms"), "call": med("total_ms")},
-        "work": {k: p0[k] for k in ("n_wedges", "n_bloom_wedges", "n_blooms", "rounds", "levels",
-                                    "support_updates", "pair_slots", "link_visits")},
-        "kernels_gbs": {k: ab[k] / (kern[k] / 1e3) / 1e9 for k in kern if kern[k] > 0},
-        "roofline": {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "algorithmic_bytes": ab[dom],
-                     "traffic": measured_traffic(dom, args.workload)},
+                   "planted_bicliques": WORKLOAD.get("nplant", 0), "seed": WORKLOAD["seed"],
+                   "parallelism": f"replicas x{ws}",
+                   "cache": "L2 flushed (256 MiB write) before every timed step and every e2e call; "
+                            "the inputs also exceed L2"},
+        **summary,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * m,
-                "d2h_bytes_per_step": 12 * m, "steps": e2e_steps},
-        "gpu_launches": int(sum(p["launches"] for p in profs)),
+                "d2h_bytes_per_step": 12 * m, "steps": e2e_steps, "equal_to_device_path": e2e_exact},
+        "gpu_launches": launches,
         "hierarchy_ms": {"order_by_phi": statistics.median(hier["order"]),
                          "k_bitruss": statistics.median(hier["k_bitruss"]), "k": k_mid},
         "clocks": clk,
         "wall_s": wall,
+        **extras,
     }
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
-    h.close()
     if dist:
         dist.destroy_process_group()
     return 0

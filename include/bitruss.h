@@ -103,6 +103,8 @@ typedef struct {
     uint64_t rounds, levels, support_updates;
     uint64_t pair_slots;   /* bloom pair slots the peel's bloom phase visited */
     uint64_t link_visits;  /* edge-bloom links the peel's incidence phase visited */
+    uint64_t scanned;      /* edge-list entries the peel's level jumps scanned (the
+                              near window, and the alive list when it is rebuilt) */
 } bt_profile;
 
 /*

@@ -69,7 +69,7 @@ class Profile(ctypes.Structure):
                 ("n_bloom_wedges", ctypes.c_uint64), ("n_blooms", ctypes.c_uint64),
                 ("rounds", ctypes.c_uint64), ("levels", ctypes.c_uint64),
                 ("support_updates", ctypes.c_uint64), ("pair_slots", ctypes.c_uint64),
-                ("link_visits", ctypes.c_uint64)]
+                ("link_visits", ctypes.c_uint64), ("scanned", ctypes.c_uint64)]
 
 
 class Graph(ctypes.Structure):

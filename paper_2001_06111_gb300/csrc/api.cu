@@ -571,6 +571,7 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
         h->last.levels = pr.levels;
         h->last.support_updates = pr.updates;
         h->last.pair_slots = pr.slots;
+        h->last.scanned = pr.scanned;
         h->last.link_visits = h->index.links;
     }
     cudaStreamSynchronize(h->stream);

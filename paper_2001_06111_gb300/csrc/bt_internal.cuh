@@ -184,7 +184,7 @@ void free_index(Index &ix, Alloc &al);
 
 // ---------------------------------------------------------------- peeling
 struct PeelResult {
-    uint64_t rounds = 0, levels = 0, updates = 0, kmax = 0, windows = 0, slots = 0;
+    uint64_t rounds = 0, levels = 0, updates = 0, kmax = 0, windows = 0, slots = 0, scanned = 0;
     uint64_t inc_phases = 0;  // rounds that ran a separate incidence phase
     int status = BT_OK;
 };

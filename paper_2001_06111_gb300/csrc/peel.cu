@@ -89,6 +89,7 @@ struct Ctl {
     unsigned long long minsup2;  // minimum over all alive edges (window rebuild)
     unsigned long long updates;
     unsigned long long slots;  // bloom pair slots visited by the bloom phase
+    unsigned long long scanned;  // edge-list entries scanned by level jumps
     unsigned long long rounds;
     unsigned long long levels;
     unsigned long long windows;
@@ -402,6 +403,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             break;
         }
         if (level_jump) {
+            if (gtid == 0) atomicAdd(&ctl->scanned, (unsigned long long)v_near);
             // L1: minimum over the near window, compacting it
             {
                 unsigned long long best = ~0ull;
@@ -443,6 +445,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             if (mn == ~0ull) {
                 // the window holds no alive edge: rebuild it from all alive edges.
                 // W1: overall minimum, compacting the alive list
+                if (gtid == 0) atomicAdd(&ctl->scanned, (unsigned long long)v_alive);
                 unsigned long long best = ~0ull;
                 for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < v_alive; i0 += nthreads) {
                     const uint32_t i = i0 + threadIdx.x;
@@ -482,6 +485,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 if (gtid == 0) ctl->n_alive[ap ^ 1u] = 0;
                 // W2: list every alive edge below the new window top (one
                 // counter atomic per warp: the list can take most edges)
+                if (gtid == 0) atomicAdd(&ctl->scanned, (unsigned long long)v_alive);
                 for (uint32_t i0 = gwarp * 32u; i0 < v_alive; i0 += nthreads) {
                     const uint32_t i = i0 + lane;
                     uint32_t e = 0;
@@ -517,6 +521,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             // with one atomic per warp; a small one per edge, which is faster
             // when only a few edges are selected.
             uint32_t sel = 0;
+            if (gtid == 0) atomicAdd(&ctl->scanned, (unsigned long long)v_near);
             if (v_near > kWarpSlotsMin) {
                 for (uint32_t i0 = gwarp * 32u; i0 < v_near; i0 += nthreads) {
                     const uint32_t i = i0 + lane;
@@ -875,6 +880,7 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     res.windows = h.windows;
     res.updates = h.updates;
     res.slots = h.slots;
+    res.scanned = h.scanned;
     res.kmax = h.kfinal;
     res.inc_phases = h.inc_phases;
     al.put(a.sup);

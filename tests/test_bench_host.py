@@ -9,11 +9,28 @@ import bench
 
 def test_algorithmic_bytes_model():
     p = {"n_wedges": 10, "n_bloom_wedges": 4, "n_blooms": 2, "n_edges": 7,
-         "link_visits": 8, "pair_slots": 5, "support_updates": 3}
+         "link_visits": 8, "pair_slots": 5, "support_updates": 3, "scanned": 11}
     ab = bench.algorithmic_bytes(p)
-    assert ab["count"] == 12 * 10 + 8 * 4 + 20 * 7
-    assert ab["emit"] == 8 * 10 + 20 * 4 + 12 * 2
-    assert ab["peel"] == 25 * 8 + 9 * 5 + 16 * 3
+    # pass A 4W + 12m, pass B 8W + 8 W2 + 8m
+    assert ab["count"] == (4 * 10 + 12 * 7) + (8 * 10 + 8 * 4 + 8 * 7)
+    # wedge ids and edge ids, twin pairs, links, bloom records
+    assert ab["emit"] == 8 * 10 + 8 * 4 + 8 * 4 + 12 * 2
+    # scanned entries, link visits, pair slots, support updates
+    assert ab["peel"] == 9 * 11 + 8 * 8 + 10 * 5 + 8 * 3
+
+
+def test_traffic_of_a_smaller_capture_scales_with_the_work(tmp_path, monkeypatch):
+    root, csrc = _fake_root(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    h = {n: hashlib.sha256((csrc / n).read_bytes()).hexdigest() for n in ("peel.cu", "csr.cu")}
+    (root / "profiles" / "k_peel-c3shape-3M.md").write_text(
+        "captured on a smaller case of the same shape, scaled to the full workload\n"
+        "| figure | value |\n|---|---|\n"
+        "| traffic_bytes_per_launch | 1000 |\n| algorithmic_bytes_per_launch | 4000 |\n"
+        f"| kernel source sha256 (csrc/peel.cu) | {h['peel.cu']} |\n"
+        f"| edge numbering sha256 (csrc/csr.cu) | {h['csr.cu']} |\n")
+    assert bench.measured_traffic("peel", "large", 40000) == 10000
+    assert bench.measured_traffic("peel", "large", None) is None
 
 
 def _fake_root(tmp_path, traffic=123456789):
