@@ -12,6 +12,9 @@ read-only support count, single-threaded peeling):
 * ``bitruss``          -- initial supports and bitruss numbers by the
   one-edge-at-a-time bottom-up peeling of Alg. 1 (BiT-BS, Section III).
 * ``support_sampled``  -- supports of selected edges only.
+* ``support_anchored`` -- supports from the butterflies whose anchor (the
+  vertex of highest priority, Def. 7) has a priority rank in a given range;
+  by Lemma 3 the ranges of a partition sum to the supports.
 * ``local_check``      -- per selected edge, the count of butterflies whose
   other edges all have phi >= phi(e), and the local h-value (the fixpoint
   property every correct phi satisfies; follows from Defs. 4-5).
@@ -61,9 +64,10 @@ def _load():
             lib.oracle_support_sampled.argtypes = [P, U64, U32, U32, P, U64, P]
             lib.oracle_bitruss.argtypes = [P, U64, U32, U32, P, P]
             lib.oracle_local_check.argtypes = [P, U64, U32, U32, P, P, U64, P, P]
+            lib.oracle_support_anchored.argtypes = [P, U64, U32, U32, ctypes.c_int, U64, U64, P]
             lib.oracle_threads.restype = ctypes.c_int
             for f in (lib.oracle_support, lib.oracle_support_sampled, lib.oracle_bitruss,
-                      lib.oracle_local_check):
+                      lib.oracle_local_check, lib.oracle_support_anchored):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -97,6 +101,19 @@ def support_sampled(edges, nU: int, nL: int, which) -> np.ndarray:
     out = np.empty(w.shape[0], dtype=np.uint64)
     _check(_load().oracle_support_sampled(e.ctypes.data, e.shape[0], nU, nL, w.ctypes.data,
                                           w.shape[0], out.ctypes.data))
+    return out
+
+
+def support_anchored(edges, nU: int, nL: int, rank_lo: int, rank_hi: int,
+                     lower_first: bool = False) -> np.ndarray:
+    """Supports counting only butterflies anchored at priority ranks in
+    [rank_lo, rank_hi): the anchor is the butterfly's vertex of highest
+    priority (Def. 7, degree then global id; global ids as in Section II, or
+    the Fig. 6 reading with lower_first).  Rank 0 is the lowest priority."""
+    e = _edges(edges)
+    out = np.empty(e.shape[0], dtype=np.uint64)
+    _check(_load().oracle_support_anchored(e.ctypes.data, e.shape[0], nU, nL, 1 if lower_first else 0,
+                                           rank_lo, rank_hi, out.ctypes.data))
     return out
 
 

@@ -25,6 +25,13 @@
  * is independent of the method it checks (BE-Index, Section IV; BiT-BU++,
  * Alg. 5).
  *
+ * A fourth routine splits the supports by the anchor of each butterfly: the
+ * butterfly's vertex of highest priority (Def. 7: degree, then global id).
+ * Lemma 3 puts every butterfly in exactly one maximal priority-obeyed bloom,
+ * the one started at that vertex, so the supports contributed by the
+ * butterflies anchored in disjoint rank ranges sum to the supports.  It is
+ * the definition a counting shard over start-vertex ranges must reproduce.
+ *
  * A third routine evaluates, for sampled edges, the local fixpoint property
  * that any correct phi satisfies (follows from Defs. 4-5): phi(e) equals the
  * largest j such that at least j butterflies through e have all their other
@@ -359,4 +366,83 @@ int oracle_local_check(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t n
     }
     og_free(&g);
     return bad ? -1 : 0;
+}
+
+/*
+ * Supports counting only the butterflies whose anchor -- the butterfly's
+ * vertex of highest priority, Def. 7: larger degree, ties broken by the
+ * larger global id -- has a priority rank in [rank_lo, rank_hi) (rank 0 is
+ * the lowest priority).  Global ids follow Section II (lower v -> v, upper
+ * u -> nL + u), or with lower_first the reading of Fig. 6 (upper u -> u,
+ * lower v -> nU + v).  Butterflies through e = (u, v) are enumerated as in
+ * support_of: w in N(v) \ {u}, x in N(u) ∩ N(w) \ {v}.
+ */
+int oracle_support_anchored(const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL, int lower_first,
+                            uint64_t rank_lo, uint64_t rank_hi, uint64_t *sup) {
+    og_t g;
+    int rc = og_build(&g, edges, m, nU, nL);
+    if (rc) return rc;
+    const uint64_t n = (uint64_t)nU + nL;
+    /* rank of every vertex: upper u at index u, lower v at index nU + v */
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (n ? n : 1));
+    uint32_t *idx = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    uint32_t *rank = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
+    if (!key || !idx || !rank) { free(key); free(idx); free(rank); og_free(&g); return -1; }
+    for (uint64_t x = 0; x < n; ++x) {
+        int upper = x < nU;
+        uint64_t deg = upper ? g.offU[x + 1] - g.offU[x] : g.offL[x - nU + 1] - g.offL[x - nU];
+        uint64_t gid = upper ? (lower_first ? x : (uint64_t)nL + x) : (lower_first ? x : x - nU);
+        key[x] = deg << 32 | gid; /* degrees and ids < 2^32 */
+        idx[x] = (uint32_t)x;
+    }
+    /* sort vertex indices by key ascending (heap sort on (key, idx)) */
+    for (uint64_t s0 = n / 2; s0-- > 0;) {
+        uint64_t r = s0;
+        for (;;) {
+            uint64_t c = 2 * r + 1;
+            if (c >= n) break;
+            if (c + 1 < n && key[idx[c + 1]] > key[idx[c]]) ++c;
+            if (key[idx[r]] >= key[idx[c]]) break;
+            uint32_t t = idx[r]; idx[r] = idx[c]; idx[c] = t;
+            r = c;
+        }
+    }
+    for (uint64_t end = n; end-- > 1;) {
+        uint32_t t = idx[0]; idx[0] = idx[end]; idx[end] = t;
+        uint64_t r = 0;
+        for (;;) {
+            uint64_t c = 2 * r + 1;
+            if (c >= end) break;
+            if (c + 1 < end && key[idx[c + 1]] > key[idx[c]]) ++c;
+            if (key[idx[r]] >= key[idx[c]]) break;
+            t = idx[r]; idx[r] = idx[c]; idx[c] = t;
+            r = c;
+        }
+    }
+    for (uint64_t r = 0; r < n; ++r) rank[idx[r]] = (uint32_t)r;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t e = 0; e < (int64_t)m; ++e) {
+        uint32_t u = (uint32_t)edges[2 * e], v = (uint32_t)edges[2 * e + 1];
+        uint64_t s = 0;
+        for (uint64_t j = g.offL[v]; j < g.offL[v + 1]; ++j) {
+            uint32_t w = g.adjL[j];
+            if (w == u) continue;
+            const uint32_t *nu = g.adjU + g.offU[u], *nw = g.adjU + g.offU[w];
+            uint64_t du = g.offU[u + 1] - g.offU[u], dw = g.offU[w + 1] - g.offU[w];
+            for (uint64_t t = 0; t < du; ++t) {
+                uint32_t x = nu[t];
+                if (x == v || find_sorted(nw, dw, x) < 0) continue;
+                /* butterfly {u, w} x {v, x}: its anchor's rank */
+                uint32_t top = rank[u];
+                if (rank[w] > top) top = rank[w];
+                if (rank[nU + v] > top) top = rank[nU + v];
+                if (rank[nU + x] > top) top = rank[nU + x];
+                s += top >= rank_lo && top < rank_hi;
+            }
+        }
+        sup[e] = s;
+    }
+    free(key); free(idx); free(rank);
+    og_free(&g);
+    return 0;
 }

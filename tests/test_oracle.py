@@ -207,3 +207,47 @@ def test_hierarchy_order_by_brute_force():
     for k in range(8):
         n = int((phi >= k).sum())
         assert sorted(order[:n].tolist()) == np.flatnonzero(phi >= k).tolist()
+
+
+def test_anchored_support_paper_example():
+    # per-anchor contributions derived by hand from Lemma 3 and Def. 7 on G
+    # (tests/golden/paper_example_anchored.txt), under both id readings
+    nU, nL, rows = pins.read_golden(os.path.join(GOLDEN, "paper_example_anchored.txt"))
+    edges = np.array([(int(r[1]), int(r[2])) for r in rows], dtype=np.int32)
+    col = lambda j: [int(r[j]) for r in rows]  # noqa: E731
+    assert oracle.support_anchored(edges, nU, nL, 8, 9).tolist() == col(3)
+    assert oracle.support_anchored(edges, nU, nL, 7, 8).tolist() == col(4)
+    assert oracle.support_anchored(edges, nU, nL, 0, 7).tolist() == [0] * len(rows)
+    assert oracle.support_anchored(edges, nU, nL, 8, 9, lower_first=True).tolist() == col(5)
+    assert oracle.support_anchored(edges, nU, nL, 0, 8, lower_first=True).tolist() == [0] * len(rows)
+
+
+@pytest.mark.parametrize("a,b", [(2, 3), (3, 5), (4, 9)])
+def test_anchored_support_biclique_closed_form(a, b):
+    # K_{a,b}, a < b: upper vertices have degree b > a, so the anchor of a
+    # butterfly {u_j, u_i} x {v_x, v_y} (j < i) is u_i (ties broken by the
+    # larger id).  Anchor u_i holds i * C(b, 2) butterflies: its own edges lie
+    # in i (b - 1) of them, each edge of a lower upper vertex u_j in b - 1.
+    # Ranks: the b lower vertices first (degree a), then u_0 .. u_{a-1}, so
+    # u_i has rank b + i.
+    e = pins.biclique(a, b)
+    for i in range(a):
+        got = oracle.support_anchored(e, a, b, b + i, b + i + 1)
+        want = np.array([i * (b - 1) if int(u) == i else (b - 1 if int(u) < i else 0) for u, _ in e])
+        assert got.tolist() == want.tolist()
+    assert (oracle.support_anchored(e, a, b, 0, b) == 0).all()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_anchored_support_partitions_sum_to_support(seed):
+    # Lemma 3: every butterfly has exactly one anchor, so the supports of the
+    # ranges of any partition of the ranks add up to the supports
+    g = synth.chunglu(120, 90, 900, 2.1, 2.4, seed=300 + seed)
+    n = g.nU + g.nL
+    rng = np.random.default_rng(seed)
+    cuts = np.sort(rng.choice(np.arange(1, n), size=5, replace=False))
+    bounds = [0, *cuts.tolist(), n]
+    for lower_first in (False, True):
+        parts = [oracle.support_anchored(g.edges, g.nU, g.nL, lo, hi, lower_first)
+                 for lo, hi in zip(bounds[:-1], bounds[1:])]
+        np.testing.assert_array_equal(np.sum(parts, axis=0), oracle.support(g.edges, g.nU, g.nL))
