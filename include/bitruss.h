@@ -156,6 +156,27 @@ int bt_index_export(bt_handle *h, bt_bloom_rec *blooms_out, uint32_t *pairs_out,
                     uint32_t *edge_deg_out);
 
 /*
+ * One part of a counting shard over start vertices (Section IV-B: every
+ * priority-obeyed wedge is enumerated from its start vertex, the vertex of
+ * highest priority, and by Lemma 3 every butterfly lies in exactly one bloom,
+ * the one started at its vertex of highest priority).  The vertices are
+ * ranked by priority (Def. 7) and cut into nparts contiguous rank ranges
+ * holding about equal numbers of priority-obeyed wedges; this call counts
+ * part `part`: support_out receives, per edge, the butterflies anchored at a
+ * vertex of that range.  The parts of one graph add up to bt_count_support's
+ * result, so processes that each count one part and sum the arrays (one
+ * reduction) obtain the supports.
+ *   part, nparts:   0 <= part < nparts.
+ *   support_out:    uint64[m] (host, or device with BT_DEVICE_PTRS), input order.
+ *   rank_lo_out, rank_hi_out: nullable; the rank range [lo, hi) counted
+ *                   (rank 0 is the lowest priority).
+ * Errors: as bt_count_support, plus BT_ERR_ARG for part >= nparts.
+ */
+int bt_count_support_part(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                          uint32_t part, uint32_t nparts, uint64_t *support_out, uint32_t *rank_lo_out,
+                          uint32_t *rank_hi_out, uint32_t flags);
+
+/*
  * Bitruss number of every edge (Defs. 4-5): counting, BE-Index build, then
  * level-synchronous batch peeling (Alg. 5; every unassigned edge with
  * support <= k is peeled in one batch, k = max(k, minimum support)).

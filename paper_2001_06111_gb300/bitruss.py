@@ -35,7 +35,7 @@ EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_
             "bt_profile_read", "bt_count_support_static", "bt_decompose_batch",
             "bt_server_create", "bt_server_destroy", "bt_server_submit", "bt_server_poll",
             "bt_server_stats_read", "bt_decompose_progressive", "bt_hierarchy", "bt_k_bitruss",
-            "bt_set_limits")
+            "bt_set_limits", "bt_count_support_part")
 
 
 class BitrussError(RuntimeError):
@@ -174,6 +174,8 @@ def load(path: str = LIB_PATH):
                                                  ctypes.POINTER(PcStats), U32]
         lib.bt_profile_enable.argtypes = [P, I]
         lib.bt_set_limits.argtypes = [P, ctypes.POINTER(Limits)]
+        lib.bt_count_support_part.argtypes = [P, P, U64, U32, U32, U32, U32, P, ctypes.POINTER(U32),
+                                              ctypes.POINTER(U32), U32]
         lib.bt_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         lib.bt_estimate_bytes.argtypes = [P, U64, U32, U32, U32, ctypes.POINTER(U64),
                                           ctypes.POINTER(U64)]
@@ -262,6 +264,21 @@ def bt_count_support(h: Handle, edges, nU: int, nL: int, support_out=None, flags
     sup, sptr = _out(import_dev, m, np.uint64, _torch_dtype("uint64"), support_out)
     _check(h, load().bt_count_support(h.ptr, ptr, m, nU, nL, sptr, flags | f))
     return sup
+
+
+def bt_count_support_part(h: Handle, edges, nU: int, nL: int, part: int, nparts: int, support_out=None,
+                          flags: int = 0):
+    """One part of a counting shard: the supports contributed by the
+    butterflies anchored in part `part` of `nparts` wedge-balanced priority-rank
+    ranges.  Returns (support u64[m], rank_lo, rank_hi); the parts of a graph
+    add up to bt_count_support's result."""
+    ptr, m, f, keep = _edges_arg(edges)
+    dev = keep if f & BT_DEVICE_PTRS else None
+    sup, sptr = _out(dev, m, np.uint64, _torch_dtype("uint64"), support_out)
+    lo, hi = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(h, load().bt_count_support_part(h.ptr, ptr, m, nU, nL, part, nparts, sptr, ctypes.byref(lo),
+                                           ctypes.byref(hi), flags | f))
+    return sup, int(lo.value), int(hi.value)
 
 
 def _phi_arg(phi):

@@ -313,6 +313,76 @@ int bt_count_support(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU
     return rc;
 }
 
+int bt_count_support_part(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
+                          uint32_t part, uint32_t nparts, uint64_t *support_out, uint32_t *rank_lo_out,
+                          uint32_t *rank_hi_out, uint32_t flags) {
+    int rc = check_args(h, edges, m, nU, nL, flags);
+    if (rc) return rc;
+    h->err.clear();
+    if (nparts == 0 || part >= nparts) return fail(h, BT_ERR_ARG, "part %u of %u parts", part, nparts);
+    if (rank_lo_out) *rank_lo_out = 0;
+    if (rank_hi_out) *rank_hi_out = 0;
+    if (m == 0) return BT_OK;
+    if (!support_out) return fail(h, BT_ERR_ARG, "support_out is NULL");
+    DeviceGuard dg(h->device);
+    bt::Alloc al = make_alloc(h);
+    call_begin(h, al, m, nU + nL);
+    Prepared P;
+    rc = prepare(h, edges, m, nU, nL, flags, P, al);
+    uint64_t *d_sup = nullptr, *d_int = nullptr, *pre = nullptr, *tot = nullptr;
+    uint32_t *bounds = nullptr;
+    if (rc == BT_OK) {
+        d_int = al.get<uint64_t>(m);
+        d_sup = (flags & BT_DEVICE_PTRS) ? support_out : al.get<uint64_t>(m);
+        pre = al.get<uint64_t>(P.g.n);
+        tot = al.get<uint64_t>(1);
+        bounds = al.get<uint32_t>(2);
+        if (al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating supports");
+    }
+    uint32_t hb[2] = {0, 0};
+    if (rc == BT_OK) {
+        // W-balanced contiguous rank ranges: part p starts at the first rank
+        // whose preceding start vertices hold at least p W / nparts wedges
+        uint64_t W = 0;
+        cudaError_t e = bt::exclusive_scan_u64(P.g.wv, pre, P.g.n, tot, al);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&W, tot, sizeof(W), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        const uint64_t t0 = (uint64_t)((unsigned __int128)W * part / nparts);
+        const uint64_t t1 = (uint64_t)((unsigned __int128)W * (part + 1) / nparts);
+        if (e == cudaSuccess) e = bt::rank_bounds(pre, P.g.n, t0, t1, bounds, al);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "splitting the start vertices");
+        if (part == 0) hb[0] = 0;
+        if (part + 1 == nparts) hb[1] = P.g.n;
+    }
+    if (rc == BT_OK) {
+        bt::CountOut co;
+        co.support = d_int;
+        cudaError_t e = bt::count_wedges(P.g, co, h->num_sms, al, h->count_nt, hb[0], hb[1]);
+        if (e == cudaSuccess) {
+            al.put(co.butterflies_dev);
+            e = bt::gather_u64(d_int, P.g.newid, d_sup, m, al);  // back to input order
+        }
+        if (e == cudaSuccess) e = deliver(h, support_out, d_sup, sizeof(uint64_t) * m, flags);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(h, e, "counting a part");
+    }
+    if (rc == BT_OK) {
+        if (rank_lo_out) *rank_lo_out = hb[0];
+        if (rank_hi_out) *rank_hi_out = hb[1];
+    }
+    al.put(d_int);
+    if (!(flags & BT_DEVICE_PTRS)) al.put(d_sup);
+    al.put(pre);
+    al.put(tot);
+    al.put(bounds);
+    release(P, al);
+    call_end(h, al);
+    cudaStreamSynchronize(h->stream);
+    return rc;
+}
+
 // Stages a u32[m] array on the device (or uses it in place with BT_DEVICE_PTRS).
 static int stage_u32(bt_handle *h, const uint32_t *src, uint64_t m, uint32_t flags, bt::Alloc &al,
                      const uint32_t **d_out, uint32_t **owned) {

@@ -155,8 +155,14 @@ struct CountOut {
     // compression); they get no links and are flagged in bit 31 inside pairs
     const uint8_t *assigned = nullptr;
 };
-// nt: count block size (256, 512 or 1024; anything else means 512)
-cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt = 512);
+// nt: count block size (256, 512 or 1024; anything else means 512).  Only
+// start vertices of rank in [lo, hi) are enumerated: the supports are then
+// those of the blooms started there (a counting shard).
+cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt = 512, uint32_t lo = 0,
+                         uint32_t hi = 0xFFFFFFFFu);
+// out[0], out[1]: the first rank r with pre[r] >= t0, resp. >= t1 (pre is a
+// non-decreasing array of n values; n when no such rank).
+cudaError_t rank_bounds(const uint64_t *pre, uint32_t n, uint64_t t0, uint64_t t1, uint32_t *out, Alloc &al);
 
 // Device-resident BE-Index (Section IV-A).
 struct Index {

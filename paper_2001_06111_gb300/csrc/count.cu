@@ -64,12 +64,13 @@ __device__ __forceinline__ uint64_t wedge_arc(const Chunk<NT> &ch, const uint64_
     return off[ch.v[vi]] + (t - ch.off[vi]);
 }
 
-__device__ __forceinline__ uint32_t next_vertex(uint32_t *queue, uint32_t n, uint32_t *s_q) {
+// Next start vertex of the rank range [lo, hi), highest rank first.
+__device__ __forceinline__ uint32_t next_vertex(uint32_t *queue, uint32_t lo, uint32_t hi, uint32_t *s_q) {
     if (threadIdx.x == 0) *s_q = atomicAdd(queue, 1u);
     __syncthreads();
     uint32_t qi = *s_q;
     __syncthreads();
-    return qi < n ? n - 1 - qi : 0xFFFFFFFFu;
+    return qi < hi - lo ? hi - 1 - qi : 0xFFFFFFFFu;
 }
 
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t *p) { return __ldcg(p); }
@@ -94,7 +95,7 @@ template <bool kIndex, int NT>
 __global__ void __launch_bounds__(NT) k_count(
     const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
     const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
-    const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
+    const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t lo, uint32_t hi,
     const uint32_t *__restrict__ vbase, uint32_t cn,
     uint32_t *cnt_all, unsigned long long *support, uint32_t *inc_cnt, uint64_t *w2v,
     uint64_t *nbv, unsigned long long *totals, uint32_t *queue, const uint8_t *__restrict__ assigned) {
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(NT) k_count(
     s_inc[threadIdx.x] = 0;
     unsigned long long bf_total = 0;
     for (;;) {
-        uint32_t u = next_vertex(queue, n, &s_q);
+        uint32_t u = next_vertex(queue, lo, hi, &s_q);
         if (u == 0xFFFFFFFFu) break;
         if (wv[u] == 0) {
             if (kIndex && threadIdx.x == 0) {
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(NT) k_emit(
     uint32_t *cnt = cnt_all + (size_t)blockIdx.x * cn;
     uint32_t *aux = aux_all + (size_t)blockIdx.x * cn;
     for (;;) {
-        uint32_t u = next_vertex(queue, n, &s_q);
+        uint32_t u = next_vertex(queue, 0u, n, &s_q);
         if (u == 0xFFFFFFFFu) break;
         if (wv[u] == 0) continue;
         const uint64_t a = off[u];
@@ -281,20 +282,23 @@ int blocks_per_sm_for(int nt) {
 }
 
 template <int NT>
-void launch_count(bool index, unsigned blocks, const Csr &g, uint32_t *cnt, unsigned long long *sup,
-                  CountOut &o, unsigned long long *totals, uint32_t *queue, cudaStream_t st) {
+void launch_count(bool index, unsigned blocks, const Csr &g, uint32_t lo, uint32_t hi, uint32_t *cnt,
+                  unsigned long long *sup, CountOut &o, unsigned long long *totals, uint32_t *queue,
+                  cudaStream_t st) {
     if (index)
-        k_count<true, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, g.vbase, g.cnt_n, cnt, sup,
-                                                  o.inc_cnt, o.w2v, o.nbv, totals, queue, o.assigned);
+        k_count<true, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, lo, hi, g.vbase, g.cnt_n, cnt,
+                                                  sup, o.inc_cnt, o.w2v, o.nbv, totals, queue, o.assigned);
     else
-        k_count<false, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, g.n, g.vbase, g.cnt_n, cnt, sup,
-                                                   nullptr, nullptr, nullptr, totals, queue, nullptr);
+        k_count<false, NT><<<blocks, NT, 0, st>>>(g.off, g.adj, g.eid, g.hv, g.pl, g.wv, lo, hi, g.vbase, g.cnt_n, cnt,
+                                                   sup, nullptr, nullptr, nullptr, totals, queue, nullptr);
 }
 
 }  // namespace
 
-cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt) {
+cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int nt, uint32_t lo, uint32_t hi) {
     const bool index = o.inc_cnt != nullptr;
+    if (hi > g.n) hi = g.n;
+    if (lo > hi) lo = hi;
     if (nt != 256 && nt != 1024) nt = 512;
     int bps = blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
@@ -309,9 +313,9 @@ cudaError_t count_wedges(const Csr &g, CountOut &o, int num_sms, Alloc &al, int 
     if (index) BT_CUDA(cudaMemsetAsync(o.inc_cnt, 0, sizeof(uint32_t) * g.m, al.stream));
     auto *sup = reinterpret_cast<unsigned long long *>(o.support);
     al.mark(kPhCount, false);
-    if (nt == 256) launch_count<256>(index, blocks, g, cnt, sup, o, totals, queue, al.stream);
-    else if (nt == 1024) launch_count<1024>(index, blocks, g, cnt, sup, o, totals, queue, al.stream);
-    else launch_count<512>(index, blocks, g, cnt, sup, o, totals, queue, al.stream);
+    if (nt == 256) launch_count<256>(index, blocks, g, lo, hi, cnt, sup, o, totals, queue, al.stream);
+    else if (nt == 1024) launch_count<1024>(index, blocks, g, lo, hi, cnt, sup, o, totals, queue, al.stream);
+    else launch_count<512>(index, blocks, g, lo, hi, cnt, sup, o, totals, queue, al.stream);
     al.launches++;
     al.mark(kPhCount, true);
     BT_CUDA(cudaGetLastError());
@@ -392,6 +396,29 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     al.put(pair_base);
     al.put(tot);
     return cudaSuccess;
+}
+
+namespace {
+__device__ __forceinline__ uint32_t first_at_least(const uint64_t *pre, uint32_t n, uint64_t t) {
+    uint32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (pre[mid] < t) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+__global__ void k_rank_bounds(const uint64_t *pre, uint32_t n, uint64_t t0, uint64_t t1, uint32_t *out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[0] = first_at_least(pre, n, t0);
+        out[1] = first_at_least(pre, n, t1);
+    }
+}
+}  // namespace
+
+cudaError_t rank_bounds(const uint64_t *pre, uint32_t n, uint64_t t0, uint64_t t1, uint32_t *out, Alloc &al) {
+    k_rank_bounds<<<1, 32, 0, al.stream>>>(pre, n, t0, t1, out);
+    al.launches++;
+    return cudaGetLastError();
 }
 
 void free_index(Index &ix, Alloc &al) {

@@ -1,6 +1,9 @@
-"""Host logic of the multi-GPU benchmark (replicas, no data-path collective):
-two gloo ranks on the CPU check the max-over-ranks timing and the whole-job
-throughput the benchmark reports."""
+"""Multi-process host logic on the CPU (gloo ranks): the benchmark's
+max-over-ranks timing and whole-job throughput (replicas, no data-path
+collective), and the single-graph counting shard's reduction (each rank
+counts the butterflies anchored in its own priority-rank range -- here with
+the CPU oracle standing in for the GPU library -- and one all-reduce sums the
+parts into the supports)."""
 import os
 import socket
 
@@ -46,3 +49,39 @@ def test_single_process_passthrough():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_throughput(1, 2_000_000, 5, 1000.0) == 10_000_000.0
+
+
+def _shard_rank_main(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import numpy as np
+
+    import oracle
+    from paper_2001_06111_gb300 import shard, synth
+    g = synth.chunglu(300, 200, 3000, 2.1, 2.4, seed=77)
+    n = g.nU + g.nL
+    bounds = np.linspace(0, n, world + 1).astype(int)
+
+    def count_part(p, P):
+        return oracle.support_anchored(g.edges, g.nU, g.nL, int(bounds[p]), int(bounds[p + 1]))
+
+    sup = shard.count_support_sharded(g.edges, g.nU, g.nL, count_part=count_part)
+    out[rank] = sup.tolist()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_counting_shard_sums_to_supports():
+    import numpy as np
+
+    import oracle
+    from paper_2001_06111_gb300 import synth
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_shard_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
+    g = synth.chunglu(300, 200, 3000, 2.1, 2.4, seed=77)
+    want = oracle.support(g.edges, g.nU, g.nL).tolist()
+    assert out[0] == want and out[1] == want
+    assert int(np.asarray(want).sum()) > 0
