@@ -61,6 +61,7 @@ typedef enum {
 /* flags */
 #define BT_DEVICE_PTRS 0x1u      /* edge/output pointers are device pointers */
 #define BT_TIE_LOWER_FIRST 0x2u  /* lower-layer global ids above upper-layer ids */
+#define BT_PC_RECOUNT 0x4u       /* bt_decompose_progressive: Alg. 7's candidate extraction */
 
 typedef struct bt_handle bt_handle;
 
@@ -325,6 +326,8 @@ typedef struct {
     uint64_t alpha;            /* eps step, ceil(k_max * tau) */
     uint64_t index_bytes_max;  /* largest compressed BE-Index of a pass (bytes, as bt_index_stats) */
     uint64_t links;            /* edge-bloom links stored, summed over passes (assigned edges get none) */
+    uint64_t dropped_edges;    /* with BT_PC_RECOUNT: candidates whose support recounted on
+                                  G_{>=eps} fell below eps, summed over passes */
 } bt_pc_stats;
 
 /*
@@ -335,10 +338,17 @@ typedef struct {
  * Lemma 10) gets a compressed BE-Index (Alg. 6: blooms keep all their twin
  * pairs, edges already assigned get no links and receive no updates) and is
  * peeled in batches; edges leaving at a level >= eps are assigned, the others
- * wait for a smaller eps.  Every edge below eps is taken in one batch level
- * eps - 1, so a pass spends one level on them.  Same results as bt_decompose
- * (Thm. 3); fewer support updates on graphs with hub edges.
+ * wait for a smaller eps.  Two readings of the extraction step:
+ *   default        every edge below eps is taken in one batch level eps - 1
+ *                  of the pass's peel, so a pass spends one level on them;
+ *   BT_PC_RECOUNT  as Alg. 7 writes it: the supports are recounted on
+ *                  G_{>=eps}, candidates whose recounted support is below
+ *                  eps are dropped before the compressed index is built, and
+ *                  the pass peels from the candidates' minimum support.
+ * Both give the results of bt_decompose (Thm. 3); they differ in the support
+ * updates and index sizes they report (Figs. 10-11).
  *   tau in (0, 1] (the paper uses 0.02 by default and suggests 0.05-0.2).
+ *   flags: BT_DEVICE_PTRS, BT_TIE_LOWER_FIRST, BT_PC_RECOUNT.
  *   support_out may be NULL; stats may be NULL.
  * Errors: as bt_decompose, plus BT_ERR_ARG for tau outside (0, 1].
  */

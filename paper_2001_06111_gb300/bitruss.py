@@ -29,6 +29,7 @@ BT_ERR_STATE = 8
 BT_ERR_TOO_LARGE = 9
 BT_DEVICE_PTRS = 0x1
 BT_TIE_LOWER_FIRST = 0x2
+BT_PC_RECOUNT = 0x4  # bt_decompose_progressive: Alg. 7's candidate extraction
 
 EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_build_index",
             "bt_index_export", "bt_decompose", "bt_estimate_bytes", "bt_profile_enable",
@@ -102,7 +103,8 @@ class PcStats(ctypes.Structure):
                 ("levels", ctypes.c_uint64), ("support_updates", ctypes.c_uint64),
                 ("candidate_edges", ctypes.c_uint64), ("wedges", ctypes.c_uint64),
                 ("k_max", ctypes.c_uint64), ("alpha", ctypes.c_uint64),
-                ("index_bytes_max", ctypes.c_uint64), ("links", ctypes.c_uint64)]
+                ("index_bytes_max", ctypes.c_uint64), ("links", ctypes.c_uint64),
+                ("dropped_edges", ctypes.c_uint64)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -477,7 +479,9 @@ def bt_profile_read(h: Handle) -> dict:
 
 def bt_decompose_progressive(h: Handle, edges, nU: int, nL: int, tau: float = 0.1,
                              support_out=None, phi_out=None, flags: int = 0, want_support: bool = True):
-    """Progressive compression (BiT-PC); returns (support or None, phi, stats)."""
+    """Progressive compression (BiT-PC); returns (support or None, phi, stats).
+    flags may add BT_PC_RECOUNT (Alg. 7's extraction: supports recounted on
+    each candidate subgraph, candidates below eps dropped before indexing)."""
     ptr, m, f, keep = _edges_arg(edges)
     dev = keep if f & BT_DEVICE_PTRS else None
     sup, sptr = (None, None)

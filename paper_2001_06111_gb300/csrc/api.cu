@@ -995,6 +995,8 @@ int bt_decompose_batch(bt_handle *h, const bt_graph *graphs, uint32_t n, const b
 int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, uint32_t nL,
                              double tau, uint64_t *support_out, uint32_t *phi_out, bt_pc_stats *stats,
                              uint32_t flags) {
+    const bool recount = flags & BT_PC_RECOUNT;
+    flags &= ~(uint32_t)BT_PC_RECOUNT;
     int rc = check_args(h, edges, m, nU, nL, flags);
     if (rc) return rc;
     h->err.clear();
@@ -1021,6 +1023,19 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
     unsigned long long *counts = al.get<unsigned long long>(2);
     uint8_t *cass_int = al.get<uint8_t>(m);   // candidate flags in internal edge order
     uint32_t *phi_c = al.get<uint32_t>(m);    // candidate phi in candidate input order
+    // Alg. 7's extraction: supports recounted on the candidates, and the
+    // candidates kept (edges, map to candidate index, map to global id, flags)
+    uint64_t *sup_r = nullptr;
+    int32_t *cand2 = nullptr;
+    uint32_t *cmap2 = nullptr, *cmapg2 = nullptr;
+    uint8_t *cass2 = nullptr;
+    if (recount) {
+        sup_r = al.get<uint64_t>(m);
+        cand2 = al.get<int32_t>(2 * m);
+        cmap2 = al.get<uint32_t>(m);
+        cmapg2 = al.get<uint32_t>(m);
+        cass2 = al.get<uint8_t>(m);
+    }
     if (rc == BT_OK && al.err != cudaSuccess) rc = cuda_fail(h, al.err, "allocating");
     uint64_t bf = 0;
     bt::Index unused;
@@ -1064,14 +1079,47 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
             rc = cuda_fail(h, e, "extracting a candidate subgraph");
             break;
         }
+        // the candidate graph the pass indexes and peels
+        const int32_t *pc_edges = cand;
+        const uint32_t *pc_map = cmap;
+        const uint8_t *pc_ass = cass;
+        uint64_t pc_n = hc[0];
+        if (hc[1] > 0 && recount) {
+            // Alg. 7, extraction: recount the supports on G_{>=eps} and drop
+            // the candidates below eps (an assigned edge never is: its
+            // phi-bitruss lies inside G_{>=eps}, so it keeps >= phi butterflies)
+            Prepared R;
+            rc = prepare(h, cand, hc[0], nU, nL, (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, R, al);
+            if (rc == BT_OK) rc = count_and_index(h, R, sup_c, false, unused, bf, al);
+            if (rc == BT_OK) {
+                unsigned long long h2[2] = {0, 0};
+                e = bt::gather_u64(sup_c, R.g.newid, sup_r, hc[0], al);  // candidate order
+                if (e == cudaSuccess)
+                    e = bt::select_candidates(cand, sup_r, hc[0], eps, cass, cand2, cmap2, cass2, counts, al);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(h2, counts, sizeof(h2), cudaMemcpyDeviceToHost, h->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+                // global ids of the kept candidates (only the h2[0] entries written)
+                if (e == cudaSuccess && h2[0]) e = bt::gather_u32(cmap, cmap2, cmapg2, h2[0], al);
+                if (e != cudaSuccess) rc = cuda_fail(h, e, "recounting a candidate subgraph");
+                st.dropped_edges += hc[0] - h2[0];
+                pc_edges = cand2;
+                pc_map = cmapg2;
+                pc_ass = cass2;
+                pc_n = h2[0];
+                hc[1] = h2[1];
+            }
+            bt::free_csr(R.g, al);
+            if (rc != BT_OK) break;
+        }
         if (hc[1] > 0) {
             // compressed BE-Index of the candidate graph (Alg. 6), then a batch
             // peel that settles every edge leaving at a level >= eps
             Prepared Q;
-            rc = prepare(h, cand, hc[0], nU, nL, (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, Q, al);
+            rc = prepare(h, pc_edges, pc_n, nU, nL, (flags & BT_TIE_LOWER_FIRST) | BT_DEVICE_PTRS, Q, al);
             bt::Index ix;
             if (rc == BT_OK) {
-                cudaError_t es = bt::scatter_u8(cass, Q.g.newid, cass_int, hc[0], al);
+                cudaError_t es = bt::scatter_u8(pc_ass, Q.g.newid, cass_int, pc_n, al);
                 if (es != cudaSuccess) rc = cuda_fail(h, es, "extracting a candidate subgraph");
             }
             if (rc == BT_OK) rc = count_and_index(h, Q, sup_c, true, ix, bf, al, cass_int);
@@ -1081,12 +1129,14 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
                 bt::PeelOpts o;
                 o.assigned = cass_int;
                 o.m_active = hc[1];
-                o.k_init = eps > 0 ? (long long)eps - 1 : 0;
+                // default reading: every edge below eps leaves at level eps - 1;
+                // Alg. 7's: the peel starts at the minimum support
+                o.k_init = (!recount && eps > 0) ? (long long)eps - 1 : 0;
                 o.assign_from = (long long)eps;
-                e = cudaMemsetAsync(phi_local, 0xFF, 4 * hc[0], h->stream);
+                e = cudaMemsetAsync(phi_local, 0xFF, 4 * pc_n, h->stream);
                 if (e == cudaSuccess) e = bt::peel(ix, sup_c, phi_local, pr, peel_sms(h), al, h->peel_seg, &o);
-                if (e == cudaSuccess) e = bt::gather_u32(phi_local, ix.newid, phi_c, hc[0], al);
-                if (e == cudaSuccess) e = bt::settle(cmap, hc[0], cass, phi_c, d_phi, d_asg, al);
+                if (e == cudaSuccess) e = bt::gather_u32(phi_local, ix.newid, phi_c, pc_n, al);
+                if (e == cudaSuccess) e = bt::settle(pc_map, pc_n, pc_ass, phi_c, d_phi, d_asg, al);
                 if (e != cudaSuccess) rc = cuda_fail(h, e, "peeling a candidate subgraph");
                 else if (pr.status == BT_ERR_OVERFLOW) rc = fail(h, BT_ERR_OVERFLOW, "a bitruss number exceeds 2^32 - 1");
                 else if (pr.status != BT_OK) rc = fail(h, pr.status, "peeling stopped: device barrier timeout or round limit");
@@ -1099,7 +1149,7 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
             st.rounds += pr.rounds;
             st.levels += pr.levels;
             st.support_updates += pr.updates;
-            st.candidate_edges += hc[0];
+            st.candidate_edges += pc_n;
         }
         if (eps == 0) break;
         eps = eps > alpha ? eps - alpha : 0;
@@ -1124,6 +1174,11 @@ int bt_decompose_progressive(bt_handle *h, const int32_t *edges, uint64_t m, uin
     al.put(counts);
     al.put(cass_int);
     al.put(phi_c);
+    al.put(sup_r);
+    al.put(cand2);
+    al.put(cmap2);
+    al.put(cmapg2);
+    al.put(cass2);
     call_end(h, al);
     if (rc == BT_OK) {
         h->last.rounds = st.rounds;

@@ -110,3 +110,52 @@ def test_pc_compressed_index_smaller_on_medium(h):
     full = bt.bt_build_index(h, g.edges, g.nU, g.nL)
     _, _, st = bt.bt_decompose_progressive(h, g.edges, g.nU, g.nL, 0.1)
     assert 0 < st["index_bytes_max"] < full["index_bytes"]
+
+
+# Alg. 7's own extraction (BT_PC_RECOUNT): supports recounted on each candidate
+# subgraph and candidates below eps dropped before the compressed index.
+
+
+@pytest.mark.parametrize("tau", TAUS)
+def test_pc_recount_paper_example(h, tau):
+    nU, nL, rows = pins.read_golden(os.path.join(GOLDEN, "paper_example_g.txt"))
+    edges = np.array([(int(r[1]), int(r[2])) for r in rows], dtype=np.int32)
+    sup, phi, st = bt.bt_decompose_progressive(h, edges, nU, nL, tau, flags=bt.BT_PC_RECOUNT)
+    assert sup.tolist() == [int(r[3]) for r in rows]
+    assert phi.tolist() == [int(r[4]) for r in rows]
+    assert st["k_max"] == 2
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_pc_recount_random_small_graphs(h, seed):
+    rng = np.random.default_rng(500 + seed)
+    nU, nL = int(rng.integers(2, 30)), int(rng.integers(2, 30))
+    g = synth.random_tiny(500 + seed, nU, nL, int(rng.integers(1, nU * nL + 1)))
+    sr, pr = oracle.bitruss(g.edges, nU, nL)
+    for tau in TAUS:
+        sup, phi, _ = bt.bt_decompose_progressive(h, g.edges, nU, nL, tau, flags=bt.BT_PC_RECOUNT)
+        np.testing.assert_array_equal(sup, sr)
+        np.testing.assert_array_equal(phi.astype(np.uint64), pr)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_pc_recount_skewed_graphs(h, seed):
+    g = synth.chunglu(1500, 1000, 15000, 2.1, 2.4, seed=700 + seed)
+    sr, pr = oracle.bitruss(g.edges, g.nU, g.nL)
+    dropped = 0
+    for tau in (0.02, 0.1):
+        sup, phi, st = bt.bt_decompose_progressive(h, g.edges, g.nU, g.nL, tau, flags=bt.BT_PC_RECOUNT)
+        np.testing.assert_array_equal(sup, sr)
+        np.testing.assert_array_equal(phi.astype(np.uint64), pr)
+        dropped += st["dropped_edges"]
+        # the recount only removes candidates: a pass indexes at most what it extracted
+        assert st["candidate_edges"] <= st["passes"] * g.m
+    assert dropped > 0  # skewed supports: some candidates fall below eps on G_{>=eps}
+
+
+def test_pc_recount_medium_sample_equals_batch_peel(h):
+    g = synth.vertex_sample(synth.medium(), 0.2, 7)
+    _, phi_bu, _ = bt.bt_decompose(h, g.edges, g.nU, g.nL)
+    for tau in (0.02, 0.1):
+        _, phi, _ = bt.bt_decompose_progressive(h, g.edges, g.nU, g.nL, tau, flags=bt.BT_PC_RECOUNT)
+        np.testing.assert_array_equal(phi, phi_bu)
