@@ -55,7 +55,8 @@ typedef enum {
     BT_ERR_NOCONVERGE = 6,  /* peeling exceeded its round limit */
     BT_ERR_CUDA = 7,        /* a CUDA runtime call failed */
     BT_ERR_STATE = 8,       /* call needs state the handle does not hold */
-    BT_ERR_TOO_LARGE = 9    /* graph exceeds bt_count_support_static's fixed capacity */
+    BT_ERR_TOO_LARGE = 9,   /* graph exceeds bt_count_support_static's fixed capacity */
+    BT_ERR_CANCELLED = 10   /* a queued serving request was cancelled (bt_server_cancel_queued) */
 } bt_status;
 
 /* flags */
@@ -399,7 +400,8 @@ int bt_k_bitruss(bt_handle *h, const uint32_t *phi, uint64_t m, uint32_t k, uint
  * batch, and with several workers batches overlap on the device.  Admission
  * uses an O(m) upper bound on a request's device bytes from its degrees
  * (priority-obeyed wedges <= sum over edges of min(d(u), d(v)), Lemma 6).
- * Large requests (config large_edges) are never batched with others, and
+ * Large requests (config large_edges) are never batched with small ones
+ * (several waiting large ones may share a batch, config large_batch), and
  * with several workers one of them serves the small requests first (passing
  * waiting large ones), so a large graph does not hold back the small requests
  * that arrive behind it; the other workers take the oldest large request
@@ -418,6 +420,8 @@ typedef struct {
                                       own; with several workers the last one serves small requests
                                       first and the others large ones first; 0 = 2^20,
                                       UINT32_MAX = no request counts as large */
+    uint32_t large_batch;          /* up to this many waiting large requests share one batch
+                                      (their peels then share rounds); 0 = 2, 1 = each alone */
 } bt_server_config;
 
 typedef struct {
@@ -441,6 +445,11 @@ typedef struct {
 int bt_server_create(bt_server **s, int device, const bt_server_config *cfg);
 /* Finish every queued request, then stop the workers and free the server. */
 int bt_server_destroy(bt_server *s);
+/* Complete every request still waiting in the queue (not yet in a batch)
+ * with status BT_ERR_CANCELLED; batches already on the GPU finish normally.
+ * *cancelled_out (nullable) receives how many were cancelled.  Used to end a
+ * measurement window on an overloaded server.  Errors: BT_ERR_ARG. */
+int bt_server_cancel_queued(bt_server *s, uint64_t *cancelled_out);
 /* Queue one graph; returns its id.  Errors: BT_ERR_ARG, BT_ERR_NOMEM. */
 int bt_server_submit(bt_server *s, const bt_graph *g, uint64_t *request_id);
 /* State of a request (wait != 0 blocks until it completes).  Once a done

@@ -27,6 +27,7 @@ BT_ERR_NOCONVERGE = 6
 BT_ERR_CUDA = 7
 BT_ERR_STATE = 8
 BT_ERR_TOO_LARGE = 9
+BT_ERR_CANCELLED = 10
 BT_DEVICE_PTRS = 0x1
 BT_TIE_LOWER_FIRST = 0x2
 BT_PC_RECOUNT = 0x4  # bt_decompose_progressive: Alg. 7's candidate extraction
@@ -36,7 +37,7 @@ EXPORTED = ("bt_create", "bt_destroy", "bt_last_error", "bt_count_support", "bt_
             "bt_profile_read", "bt_count_support_static", "bt_decompose_batch",
             "bt_server_create", "bt_server_destroy", "bt_server_submit", "bt_server_poll",
             "bt_server_stats_read", "bt_decompose_progressive", "bt_hierarchy", "bt_k_bitruss",
-            "bt_set_limits", "bt_count_support_part")
+            "bt_set_limits", "bt_count_support_part", "bt_server_cancel_queued")
 
 
 class BitrussError(RuntimeError):
@@ -110,7 +111,7 @@ class PcStats(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("workers", ctypes.c_uint32),
                 ("max_batch_graphs", ctypes.c_uint32), ("flags", ctypes.c_uint32),
-                ("large_edges", ctypes.c_uint32)]
+                ("large_edges", ctypes.c_uint32), ("large_batch", ctypes.c_uint32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -172,6 +173,7 @@ def load(path: str = LIB_PATH):
         lib.bt_server_submit.argtypes = [P, ctypes.POINTER(Graph), ctypes.POINTER(U64)]
         lib.bt_server_poll.argtypes = [P, U64, I, ctypes.POINTER(RequestInfo)]
         lib.bt_server_stats_read.argtypes = [P, ctypes.POINTER(ServerStats)]
+        lib.bt_server_cancel_queued.argtypes = [P, ctypes.POINTER(U64)]
         lib.bt_decompose_progressive.argtypes = [P, P, U64, U32, U32, ctypes.c_double, P, P,
                                                  ctypes.POINTER(PcStats), U32]
         lib.bt_profile_enable.argtypes = [P, I]
@@ -406,9 +408,9 @@ class Server:
     request keeps its edge array and outputs alive until it completes."""
 
     def __init__(self, device: int = 0, memory_budget_bytes: int = 0, workers: int = 0,
-                 max_batch_graphs: int = 0, flags: int = 0, large_edges: int = 0):
+                 max_batch_graphs: int = 0, flags: int = 0, large_edges: int = 0, large_batch: int = 0):
         lib = load()
-        cfg = ServerConfig(memory_budget_bytes, workers, max_batch_graphs, flags, large_edges)
+        cfg = ServerConfig(memory_budget_bytes, workers, max_batch_graphs, flags, large_edges, large_batch)
         p = ctypes.c_void_p()
         rc = lib.bt_server_create(ctypes.byref(p), device, ctypes.byref(cfg))
         if rc != BT_OK:
@@ -441,6 +443,14 @@ class Server:
             _, sup, phi = self._live.pop(rid)
             return d, (sup, phi)
         return d, None
+
+    def cancel_queued(self) -> int:
+        """Cancel every request still waiting in the queue; returns how many."""
+        n = ctypes.c_uint64()
+        rc = load().bt_server_cancel_queued(self.ptr, ctypes.byref(n))
+        if rc != BT_OK:
+            raise BitrussError(rc, "bt_server_cancel_queued failed")
+        return int(n.value)
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -136,17 +136,21 @@ struct bt_server {
                     return in_flight_bytes + bytes + r->bytes + std::max(cmax, r->cnt_bytes) <=
                            cfg.memory_budget_bytes;
                 };
+                // the oldest waiting large requests, up to large_batch of them
                 const auto take_large = [&]() {
-                    for (auto it = queue.begin(); it != queue.end(); ++it)
-                        if (is_large(*it)) {
-                            if (!fits(*it)) return false;  // the oldest large one waits for memory
-                            bytes += (*it)->bytes;
-                            cmax = std::max(cmax, (*it)->cnt_bytes);
-                            batch.push_back(*it);
-                            queue.erase(it);
-                            return true;
+                    const uint32_t cap = cfg.large_batch ? cfg.large_batch : 1u;
+                    for (auto it = queue.begin(); it != queue.end() && batch.size() < cap;) {
+                        if (!is_large(*it)) {
+                            ++it;
+                            continue;
                         }
-                    return false;
+                        if (!fits(*it)) break;  // the oldest large one waits for memory
+                        bytes += (*it)->bytes;
+                        cmax = std::max(cmax, (*it)->cnt_bytes);
+                        batch.push_back(*it);
+                        it = queue.erase(it);
+                    }
+                    return !batch.empty();
                 };
                 const auto take_small = [&](bool stop_at_large) {
                     for (auto it = queue.begin(); it != queue.end();) {
@@ -197,8 +201,8 @@ struct bt_server {
             // fixed schedules: the batch autotuner would time candidates on
             // the request path whenever a new batch shape appears
             bt_tune tune{};
-            const bool alone_large = batch.size() == 1 && batch[0]->g.m >= cfg.large_edges;
-            tune.count_threads = alone_large ? 1024 : 256;
+            const bool large = batch[0]->g.m >= cfg.large_edges;  // batches are all large or all small
+            tune.count_threads = large ? 1024 : 256;
             tune.peel_item = 32;
             bt_batch_stats bs{};
             rc = bt_decompose_batch(h, graphs.data(), (uint32_t)graphs.size(), &tune, &bs,
@@ -243,6 +247,7 @@ int bt_server_create(bt_server **out, int device, const bt_server_config *cfg) {
     if (!s->cfg.memory_budget_bytes) s->cfg.memory_budget_bytes = 120ull << 30;
     if (!s->cfg.workers) s->cfg.workers = 2;
     if (!s->cfg.large_edges) s->cfg.large_edges = 1u << 20;
+    if (!s->cfg.large_batch) s->cfg.large_batch = 2;
     if (s->cfg.flags & ~(uint32_t)BT_TIE_LOWER_FIRST) {
         delete s;
         return BT_ERR_ARG;
@@ -282,6 +287,25 @@ int bt_server_destroy(bt_server *s) {
     for (bt_handle *h : s->handles) bt_destroy(h);
     for (auto &kv : s->reqs) delete kv.second;
     delete s;
+    return BT_OK;
+}
+
+int bt_server_cancel_queued(bt_server *s, uint64_t *cancelled_out) {
+    if (!s) return BT_ERR_ARG;
+    uint64_t n = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        const double t = now_s();
+        for (Request *r : s->queue) {
+            r->t_done = t;
+            r->status = BT_ERR_CANCELLED;
+            s->stats.completed++;
+            ++n;
+        }
+        s->queue.clear();
+    }
+    s->cv_done.notify_all();
+    if (cancelled_out) *cancelled_out = n;
     return BT_OK;
 }
 

@@ -112,3 +112,37 @@ def test_nonblocking_polls_while_batches_complete():
         assert info["latency_seconds"] >= info["queue_seconds"] >= 0
         np.testing.assert_array_equal(sup, sr)
         np.testing.assert_array_equal(phi.astype(np.uint64), pr)
+
+
+def test_cancel_queued_requests():
+    """Requests still waiting when the queue is cancelled complete with
+    BT_ERR_CANCELLED; the ones already in a batch finish exactly."""
+    build.build()
+    big = synth.vertex_sample(synth.medium(), 0.5, 3)  # keeps the one worker busy
+    small = [synth.batch_graph(400 + i, hi=5000) for i in range(20)]
+    with bt.Server(0, workers=1) as srv:
+        ids = [srv.submit(big.edges, big.nU, big.nL)]
+        ids += [srv.submit(g.edges, g.nU, g.nL) for g in small]
+        time.sleep(0.05)
+        n = srv.cancel_queued()
+        res = [srv.poll(i, wait=True) for i in ids]
+    assert n >= 1
+    statuses = [info["status"] for info, _ in res]
+    assert statuses.count(bt.BT_ERR_CANCELLED) == n
+    for (info, (_, phi)), g in zip(res, [big] + small):
+        if info["status"] == bt.BT_OK and g.m <= 20000:
+            np.testing.assert_array_equal(phi.astype(np.uint64), oracle.bitruss(g.edges, g.nU, g.nL)[1])
+
+
+def test_large_requests_share_a_batch(alone):
+    """With large_batch = 2, large requests waiting behind a busy worker are
+    decomposed together, each exactly as alone."""
+    large = [synth.vertex_sample(synth.medium(), 0.3, s) for s in (5, 6, 8)]
+    with bt.Server(0, workers=1, large_edges=30000, large_batch=2) as srv:
+        ids = [srv.submit(g.edges, g.nU, g.nL) for g in large]
+        res = [srv.poll(i, wait=True) for i in ids]
+        st = srv.stats()
+    assert st["max_batch_graphs"] == 2
+    for (info, (_, phi)), g in zip(res, large):
+        assert info["status"] == bt.BT_OK
+        np.testing.assert_array_equal(phi, alone(g.edges, g.nU, g.nL)[1])
