@@ -362,7 +362,10 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     ix.pairs = al.get<uint2>(ix.w2);
     ix.inc = al.get<uint2>(ix.links);
     uint32_t *inc_fill = al.get<uint32_t>(m);
-    int bps = blocks_per_sm_for(nt);
+    // 1024-thread emit blocks: one per SM, so that half as many pairs of
+    // dense per-block arrays compete for L2 (measured 5-20 % faster than two
+    // per SM; the count kernel keeps two per SM, where one measured slower)
+    int bps = nt == 1024 ? 1 : blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
     uint32_t *cnt = al.get<uint32_t>((size_t)blocks * g.cnt_n);
     uint32_t *aux = al.get<uint32_t>((size_t)blocks * g.cnt_n);
