@@ -56,7 +56,7 @@ UNIT = "edges/s"
 # CPU oracle decomposes: the baseline leg (one sample) and the reference arm
 # (one sample per step), sized to a few to tens of seconds of oracle time
 CPU_SAMPLE_FRAC = {"large": 0.07, "medium": 0.3, "small": 1.0}
-REF_SAMPLE_FRAC = {"large": 0.05, "medium": 0.2, "small": 1.0}
+REF_SAMPLE_FRAC = {"large": 0.04, "medium": 0.2, "small": 1.0}
 
 
 def gen_workload(w):
