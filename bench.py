@@ -675,7 +675,7 @@ def main():
     # end-to-end through the C ABI with host buffers: the edge copy in and the
     # support and phi copies out are inside each timed call; L2 flushed before
     # each call (outside the timed interval), as for the device-resident steps
-    e2e_steps = min(2, args.steps)
+    e2e_steps = 1  # one full step through host buffers (a 30M-edge step takes ~23 s)
     e2e_s = 0.0
     for _ in range(e2e_steps):
         flush.fill_(1)
