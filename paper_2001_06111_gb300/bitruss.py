@@ -82,7 +82,8 @@ class Graph(ctypes.Structure):
 
 class Limits(ctypes.Structure):
     _fields_ = [("peel_round_limit", ctypes.c_uint64), ("barrier_timeout_ns", ctypes.c_uint64),
-                ("hold_barrier", ctypes.c_uint64), ("fail_alloc_at", ctypes.c_uint64)]
+                ("hold_barrier", ctypes.c_uint64), ("fail_alloc_at", ctypes.c_uint64),
+                ("join_cap", ctypes.c_uint32), ("block_links", ctypes.c_uint32)]
 
 
 class Tune(ctypes.Structure):
@@ -470,10 +471,11 @@ class Server:
 
 
 def bt_set_limits(h: Handle, peel_round_limit: int = 0, barrier_timeout_ns: int = 0,
-                  hold_barrier: int = 0, fail_alloc_at: int = 0) -> None:
+                  hold_barrier: int = 0, fail_alloc_at: int = 0, join_cap: int = 0,
+                  block_links: int = 0) -> None:
     """Diagnostic limits and host-side fault injection for later calls on h
     (all zero: the defaults).  See bt_set_limits in include/bitruss.h."""
-    lim = Limits(peel_round_limit, barrier_timeout_ns, hold_barrier, fail_alloc_at)
+    lim = Limits(peel_round_limit, barrier_timeout_ns, hold_barrier, fail_alloc_at, join_cap, block_links)
     _check(h, load().bt_set_limits(h.ptr, ctypes.byref(lim)))
 
 

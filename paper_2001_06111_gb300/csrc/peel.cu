@@ -119,6 +119,8 @@ struct PeelArgs {
     uint64_t round_limit;
     unsigned long long barrier_timeout_ns;
     unsigned long long hold_barrier;  // 0, or n: block 0 skips its arrival at barrier n (from 1)
+    uint32_t join_cap;     // edges a block lists in a bloom phase (<= kJoinCap)
+    uint32_t block_links;  // links of the listed edges the block stage kills itself (<= kBlockLinks)
     // progressive compression: peel only the m_active unassigned edges, start
     // at level k_init, and record phi only for levels >= assign_from
     uint64_t m_active;
@@ -322,7 +324,7 @@ template <uint32_t kSeg>
 __device__ __forceinline__ void join_next(const PeelArgs &a, uint32_t e, uint32_t q, long long k,
                                           uint32_t *s_je, uint32_t *s_jn) {
     const uint32_t slot = atomicAdd(s_jn, 1u);
-    if (slot < kJoinCap) {
+    if (slot < a.join_cap) {
         s_je[slot] = e;
     } else {
         join_batch(a, e, q, k);
@@ -699,7 +701,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             // the block kills the twin pairs of the edges it listed
             __syncthreads();
             const uint32_t njr = s_jn;
-            const uint32_t nj = njr < kJoinCap ? njr : kJoinCap;
+            const uint32_t nj = njr < a.join_cap ? njr : a.join_cap;
             if (nj > 0) {
                 uint32_t e = 0, d = 0;
                 uint64_t ib = 0;
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     join_batch(a, e, q, L.k);
                     ib = a.inc_off[e];
                     const uint64_t dl = a.inc_off[e + 1] - ib;
-                    d = dl > kBlockLinks ? kBlockLinks + 1u : (uint32_t)dl;  // longer lists are queued
+                    d = dl > a.block_links ? a.block_links + 1u : (uint32_t)dl;  // longer lists are queued
                 }
                 uint32_t total = 0;
                 const uint32_t off = dev::block_excl_scan<uint32_t>(d, &total);
@@ -716,11 +718,11 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     s_joff[threadIdx.x] = off;
                     s_jd[threadIdx.x] = d;
                     s_jib[threadIdx.x] = ib;
-                    if (off + d > kBlockLinks) push_items<kSeg>(a, e, q & 1u, ib, a.inc_off[e + 1]);
+                    if (off + d > a.block_links) push_items<kSeg>(a, e, q & 1u, ib, a.inc_off[e + 1]);
                 }
                 if (threadIdx.x == 0) atomicAdd(&ctl->n_edges[q % 3u], nj);
                 __syncthreads();
-                const uint32_t lim = total < kBlockLinks ? total : kBlockLinks;
+                const uint32_t lim = total < a.block_links ? total : a.block_links;
                 uint2 l[2];
                 uint32_t B[2];
                 bool won[2];
@@ -731,7 +733,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     l[r] = make_uint2(0u, 0u);
                     if (x < lim) {
                         const uint32_t j = dev::last_le_u32(s_joff, nj, x);
-                        if (s_joff[j] + s_jd[j] <= kBlockLinks) {
+                        if (s_joff[j] + s_jd[j] <= a.block_links) {
                             won[r] = true;
                             l[r] = a.inc[s_jib[j] + (x - s_joff[j])];
                         }
@@ -839,6 +841,8 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
         a.round_limit = rl;
         a.barrier_timeout_ns = (lim && lim->barrier_timeout_ns) ? lim->barrier_timeout_ns : kBarrierTimeoutNs;
         a.hold_barrier = lim ? lim->hold_barrier : 0;
+        a.join_cap = (lim && lim->join_cap && lim->join_cap < kJoinCap) ? lim->join_cap : kJoinCap;
+        a.block_links = (lim && lim->block_links && lim->block_links < kBlockLinks) ? lim->block_links : kBlockLinks;
     }
     a.m_active = (opts && opts->assigned) ? opts->m_active : m;
     a.k_init = opts ? opts->k_init : 0;

@@ -250,3 +250,25 @@ def test_medium_vertex_sample_exact(h):
     workload (the sampling of the paper's scalability study, Section VI)."""
     g = synth.vertex_sample(synth.medium(), 0.2, 7)
     assert_parity(h, g.edges, g.nU, g.nL)
+
+
+@pytest.mark.parametrize("join_cap,block_links", [(1, 2), (3, 16), (8, 64), (768, 2)])
+def test_overflow_paths_exact(h, join_cap, block_links):
+    """The paths large graphs take, forced on small ones (bt_set_limits): a
+    block that lists more joining edges than its cap lets the others queue
+    their own links, and link lists longer than the block stage takes become
+    incidence items.  Results stay bit-exact against the oracle."""
+    graphs = [synth.small(), synth.chunglu(600, 400, 6000, 2.2, 2.4, seed=42),
+              synth.Graph(pins.biclique(40, 50), 40, 50)]
+    try:
+        bt.bt_set_limits(h, join_cap=join_cap, block_links=block_links)
+        for g in graphs:
+            assert_parity(h, g.edges, g.nU, g.nL)
+        # the batch peel takes the same paths
+        outs, _ = bt.bt_decompose_batch(h, [(g.edges, g.nU, g.nL) for g in graphs])
+        for (sup, phi), g in zip(outs, graphs):
+            sr, pr = oracle.bitruss(g.edges, g.nU, g.nL)
+            np.testing.assert_array_equal(sup, sr)
+            np.testing.assert_array_equal(phi.astype(np.uint64), pr)
+    finally:
+        bt.bt_set_limits(h)
