@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/bitruss.h).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -42,7 +43,29 @@ struct Alloc {
     // null.  fail_alloc_at = n > 0 makes allocation number n of this call fail.
     const bt_limits *limits = nullptr;
     uint64_t n_allocs = 0;
+    // NVTX push/pop ranges of the phases, nested call > csr, count, emit,
+    // peel (host-side issue order; no-ops unless a profiler is attached).
+    // Ranges an early error return left open are popped when the call's
+    // allocator goes away, so the thread's range stack stays balanced.
+    struct NvtxStack {
+        int open = 0;
+        NvtxStack() = default;
+        NvtxStack(const NvtxStack &) = delete;
+        NvtxStack(NvtxStack &&o) noexcept : open(o.open) { o.open = 0; }
+        ~NvtxStack() {
+            for (; open > 0; --open) nvtxRangePop();
+        }
+    } nvtx;
     void mark(int phase, bool end) {
+        static const char *const kNames[kNumPhases] = {"bitruss: csr", "bitruss: count", "bitruss: emit",
+                                                       "bitruss: peel", "bitruss: call"};
+        if (!end) {
+            nvtxRangePushA(kNames[phase]);
+            ++nvtx.open;
+        } else if (nvtx.open > 0) {
+            nvtxRangePop();
+            --nvtx.open;
+        }
         if (prof && prof->on) {
             cudaEventRecord(prof->ev[2 * phase + (end ? 1 : 0)], stream);
             prof->used[phase] = true;
