@@ -18,8 +18,11 @@
 // batch autotuner from 256, 512, 1024): a block scan of the per-arc
 // prefix lengths flattens the chunk's wedges, so every thread handles whole
 // wedges regardless of the degree skew.  Counters are a dense per-block
-// array indexed by rank, kept at zero between vertices (it is reset by the
-// same wedge walk that filled it).
+// array indexed by rank, kept at zero between vertices: when u has fewer
+// than 2^16 lower-ranked neighbours a counter's word also counts its readers
+// in pass B and the last reader clears it; otherwise a third walk (pass C)
+// clears the counters.  Emit keeps one 64-bit word per counter (count and
+// claimed bloom) so each wedge touches one memory sector per walk.
 #include "bt_device.cuh"
 #include "bt_internal.cuh"
 
@@ -91,6 +94,22 @@ __device__ void pass_count(Chunk<NT> &ch, const uint64_t *off, const uint32_t *a
     }
 }
 
+// Pass A on emit's packed words (count in the low 32 bits).
+template <int NT>
+__device__ void pass_count64(Chunk<NT> &ch, const uint64_t *off, const uint32_t *adj,
+                             const uint32_t *eid, const uint32_t *pl, uint64_t a, uint32_t h,
+                             unsigned long long *cw, uint32_t vb) {
+    for (uint32_t c0 = 0; c0 < h; c0 += NT) {
+        uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
+        for (uint32_t t = threadIdx.x; t < T; t += NT) {
+            uint32_t vi;
+            uint64_t arc = wedge_arc(ch, off, t, vi);
+            atomicAdd(&cw[adj[arc] - vb], 1ull);
+        }
+        __syncthreads();
+    }
+}
+
 template <bool kIndex, int NT>
 __global__ void __launch_bounds__(NT) k_count(
     const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
@@ -123,6 +142,11 @@ __global__ void __launch_bounds__(NT) k_count(
         const uint32_t h = hv[u];
         const uint32_t vb = vbase ? vbase[u] : 0u;
         pass_count(ch, off, adj, eid, pl, a, h, cnt, vb);
+        // a counter never exceeds h (one per middle vertex): when h < 2^16 the
+        // count keeps the low half of its word and pass B counts its readers
+        // in the high half, so the last reader clears the word (no pass C)
+        const bool packed = h < 0x10000u;
+        unsigned long long nb_local = 0;
         // pass B: attribute c-1 to both edges of every wedge in a bloom
         unsigned long long w2_local = 0;
         for (uint32_t c0 = 0; c0 < h; c0 += NT) {
@@ -130,7 +154,22 @@ __global__ void __launch_bounds__(NT) k_count(
             for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
-                uint32_t c = ld_cg(&cnt[adj[arc] - vb]);
+                uint32_t *cp = &cnt[adj[arc] - vb];
+                uint32_t c;
+                if (packed) {
+                    const uint32_t old = atomicAdd(cp, 1u << 16);
+                    c = old & 0xFFFFu;
+                    if ((old >> 16) + 1u == c) {
+                        // the last of the c wedges: the bloom is counted once
+                        *cp = 0u;
+                        if (c >= 2) {
+                            ++nb_local;
+                            bf_total += (unsigned long long)c * (c - 1) / 2;
+                        }
+                    }
+                } else {
+                    c = ld_cg(cp);
+                }
                 if (c >= 2) {
                     uint32_t evw = eid[arc];
                     atomicAdd(&support[evw], (unsigned long long)(c - 1));
@@ -155,8 +194,7 @@ __global__ void __launch_bounds__(NT) k_count(
             __syncthreads();
         }
         // pass C: reset counters; the first thread to clear a bloom counts it
-        unsigned long long nb_local = 0;
-        for (uint32_t c0 = 0; c0 < h; c0 += NT) {
+        for (uint32_t c0 = 0; c0 < (packed ? 0u : h); c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
             for (uint32_t t = threadIdx.x; t < T; t += NT) {
                 uint32_t vi;
@@ -183,14 +221,17 @@ __global__ void __launch_bounds__(NT) k_count(
 }
 
 // Emit the index: blooms (bloom number, first pair), twin pairs and the
-// per-edge link lists.  aux_all is a second dense per-block array.
+// per-edge link lists.  The dense per-block array holds one 64-bit word per
+// end vertex: the wedge count in the low half and, once the bloom is claimed,
+// 2 + its index among the vertex's blooms in the high half, so a wedge reads
+// and updates one word (one memory sector) in every pass.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_emit(
     const uint64_t *__restrict__ off, const uint32_t *__restrict__ adj,
     const uint32_t *__restrict__ eid, const uint32_t *__restrict__ hv,
     const uint32_t *__restrict__ pl, const uint64_t *__restrict__ wv, uint32_t n,
     const uint32_t *__restrict__ vbase, uint32_t cn,
-    uint32_t *cnt_all, uint32_t *aux_all, const uint64_t *__restrict__ bloom_base,
+    unsigned long long *cw_all, const uint64_t *__restrict__ bloom_base,
     const uint64_t *__restrict__ pair_base, const uint64_t *__restrict__ inc_off,
     uint32_t *inc_fill, uint32_t *bloom_k, uint32_t *bloom_off, uint2 *pairs,
     uint2 *inc, uint32_t *queue, const uint8_t *__restrict__ assigned) {
@@ -199,8 +240,7 @@ __global__ void __launch_bounds__(NT) k_emit(
     // bloom count (high 32 bits) and pair count (low 32 bits) of the vertex,
     // advanced by one atomic so that pair ranges follow bloom ids
     __shared__ unsigned long long s_alloc;
-    uint32_t *cnt = cnt_all + (size_t)blockIdx.x * cn;
-    uint32_t *aux = aux_all + (size_t)blockIdx.x * cn;
+    unsigned long long *cw = cw_all + (size_t)blockIdx.x * cn;
     for (;;) {
         uint32_t u = next_vertex(queue, 0u, n, &s_q);
         if (u == 0xFFFFFFFFu) break;
@@ -211,7 +251,7 @@ __global__ void __launch_bounds__(NT) k_emit(
         const uint64_t pb = pair_base[u];
         const uint32_t vb = vbase ? vbase[u] : 0u;
         if (threadIdx.x == 0) s_alloc = 0;
-        pass_count(ch, off, adj, eid, pl, a, h, cnt, vb);
+        pass_count64(ch, off, adj, eid, pl, a, h, cw, vb);
         // claim: one thread per bloom allocates its id and pair range
         for (uint32_t c0 = 0; c0 < h; c0 += NT) {
             uint32_t T = load_chunk(ch, adj, eid, pl, a, h, c0);
@@ -219,17 +259,18 @@ __global__ void __launch_bounds__(NT) k_emit(
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 const uint32_t w = adj[arc] - vb;  // counter index
-                uint32_t c = ld_cg(&cnt[w]);
-                // a single wedge is the only reader of its counter: clear it now
-                if (c == 1u) cnt[w] = 0u;
-                if (c >= 2 && atomicCAS(&aux[w], 0u, 1u) == 0u) {
+                const unsigned long long x = __ldcg(&cw[w]);
+                const uint32_t c = (uint32_t)x;
+                // a single wedge is the only reader of its word: clear it now
+                if (c == 1u) cw[w] = 0ull;
+                if (c >= 2 && atomicCAS(&cw[w], (unsigned long long)c, 1ull << 32 | c) == (unsigned long long)c) {
                     unsigned long long old = atomicAdd(&s_alloc, (1ull << 32) | c);
                     uint32_t j = (uint32_t)(old >> 32);
                     uint32_t p = (uint32_t)old;
                     uint64_t B = bb + j;
                     bloom_k[B] = c;
                     bloom_off[B] = (uint32_t)(pb + p);
-                    atomicExch(&aux[w], j + 2u);
+                    atomicExch(&cw[w], (unsigned long long)(j + 2u) << 32 | c);
                 }
             }
             __syncthreads();
@@ -241,13 +282,14 @@ __global__ void __launch_bounds__(NT) k_emit(
                 uint32_t vi;
                 uint64_t arc = wedge_arc(ch, off, t, vi);
                 const uint32_t w = adj[arc] - vb;  // counter index
-                uint32_t x = ld_cg(&aux[w]);
+                const uint32_t x = (uint32_t)(__ldcg(&cw[w]) >> 32);
                 if (x >= 2) {
                     uint64_t B = bb + (x - 2);
-                    uint32_t pos = atomicSub(&cnt[w], 1u) - 1u;
-                    // the last wedge of the bloom comes after every read of
-                    // aux[w] (each precedes its own decrement): clear it
-                    if (pos == 0u) aux[w] = 0u;
+                    // the low half counts down the bloom's wedges still to place
+                    uint32_t pos = (uint32_t)atomicAdd(&cw[w], ~0ull) - 1u;
+                    // the last wedge of the bloom comes after every read of the
+                    // word (each precedes its own decrement): clear it
+                    if (pos == 0u) cw[w] = 0ull;
                     uint32_t slot = ld_cg(&bloom_off[B]) + pos;
                     uint32_t euv = ch.e[vi], evw = eid[arc];
                     const bool fu = assigned && assigned[euv], fw = assigned && assigned[evw];
@@ -367,20 +409,18 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     // per SM; the count kernel keeps two per SM, where one measured slower)
     int bps = nt == 1024 ? 1 : blocks_per_sm_for(nt);
     unsigned blocks = (unsigned)(num_sms * bps);
-    uint32_t *cnt = al.get<uint32_t>((size_t)blocks * g.cnt_n);
-    uint32_t *aux = al.get<uint32_t>((size_t)blocks * g.cnt_n);
+    unsigned long long *cw = al.get<unsigned long long>((size_t)blocks * g.cnt_n);
     uint32_t *queue = al.get<uint32_t>(1);
     if (al.err != cudaSuccess) return al.err;
     uint32_t w2_32 = (uint32_t)ix.w2;
     BT_CUDA(cudaMemcpyAsync(ix.bloom_off + ix.nb, &w2_32, sizeof(uint32_t), cudaMemcpyHostToDevice,
                             stream));
     BT_CUDA(cudaMemsetAsync(inc_fill, 0, sizeof(uint32_t) * m, al.stream));
-    BT_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)blocks * g.cnt_n, al.stream));
-    BT_CUDA(cudaMemsetAsync(aux, 0, sizeof(uint32_t) * (size_t)blocks * g.cnt_n, al.stream));
+    BT_CUDA(cudaMemsetAsync(cw, 0, sizeof(unsigned long long) * (size_t)blocks * g.cnt_n, al.stream));
     BT_CUDA(cudaMemsetAsync(queue, 0, sizeof(uint32_t), al.stream));
     al.mark(kPhEmit, false);
 #define BT_EMIT_ARGS                                                                         \
-    g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, g.vbase, g.cnt_n, cnt, aux, bloom_base, pair_base, ix.inc_off,  \
+    g.off, g.adj, g.eid, g.hv, g.pl, g.wv, n, g.vbase, g.cnt_n, cw, bloom_base, pair_base, ix.inc_off,  \
         inc_fill, ix.bloom_k, ix.bloom_off, ix.pairs, ix.inc, queue, c.assigned
     if (nt == 256) k_emit<256><<<blocks, 256, 0, al.stream>>>(BT_EMIT_ARGS);
     else if (nt == 1024) k_emit<1024><<<blocks, 1024, 0, al.stream>>>(BT_EMIT_ARGS);
@@ -391,8 +431,7 @@ cudaError_t emit_index(const Csr &g, const CountOut &c, Index &ix, int num_sms, 
     BT_CUDA(cudaGetLastError());
     // the host copy of w2_32 must outlive the async copy
     BT_CUDA(cudaStreamSynchronize(stream));
-    al.put(cnt);
-    al.put(aux);
+    al.put(cw);
     al.put(queue);
     al.put(inc_fill);
     al.put(bloom_base);
