@@ -226,11 +226,11 @@ int bt_profile_read(const bt_handle *h, bt_profile *out);
  *   fail_alloc_at:      n > 0: inside each call, device allocation number n
  *                       (counted from 1) fails as if the device were out of
  *                       memory; the call returns BT_ERR_NOMEM.
- *   join_cap:           n > 0: a peel block lists at most n (instead of 768)
+ *   join_cap:           n > 0: a peel block lists at most n (instead of 640)
  *                       of the edges that join the next batch during its
  *                       bloom phase; the others queue their own links.
  *   block_links:        n > 0: a peel block's kill stage handles at most n
- *                       (instead of 1,536) links itself; longer lists become
+ *                       (instead of 1,280) links itself; longer lists become
  *                       incidence items.  (These two change no result; they
  *                       make small graphs take the paths large ones take.)
  * limits == NULL restores every default.  Errors: BT_ERR_ARG (h NULL).

@@ -50,7 +50,7 @@
 namespace bt {
 namespace {
 
-constexpr int kPeelThreads = 768;  // 80 registers a thread, no spills
+constexpr int kPeelThreads = 640;  // 96 registers a thread, no spills in either instantiation
 // entries per work item: SEG = 32 or 64 (template parameter picked by the
 // batch autotuner); each lane handles SEG / 32 entries with their loads and
 // atomics issued together.
@@ -242,17 +242,6 @@ __device__ __forceinline__ void push_near(const PeelArgs &a, uint32_t e, uint32_
     a.near[nq][atomicAdd(&a.ctl->n_near[nq], 1u)] = e;
 }
 
-// Subtract dec from support(e); list e in the near window when it falls
-// below khi.  Returns true when this decrement takes e from > k to <= k, i.e.
-// e joins the next batch (exactly one decrement does).
-__device__ __forceinline__ bool decrement(const PeelArgs &a, uint32_t e, long long dec, const Lvl &L) {
-    const long long old = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.sup[e]),
-                                               (unsigned long long)(-dec));
-    const long long now = old - dec;
-    if (old >= L.khi && now < L.khi) push_near(a, e, L.nq);
-    return old > L.k && now <= L.k;
-}
-
 // Window above the current minimum: narrow enough that a level jump scans few
 // edges at high levels (dense cores hold many edges in a support range), wide
 // enough that rebuilds from the full alive list stay rare.
@@ -333,36 +322,54 @@ __device__ __forceinline__ void join_next(const PeelArgs &a, uint32_t e, uint32_
     }
 }
 
-// Bloom phase of round r, one pair slot (died stamp d, members pr) of a bloom
-// with c pairs killed this round and bloom number kB at round start.
-template <uint32_t kSeg>
-__device__ __forceinline__ void apply_slot(const PeelArgs &a, uint32_t d, uint2 pr, uint32_t c, uint32_t kB,
-                                           const Lvl &L, uint32_t round, unsigned long long &upd,
-                                           uint32_t *s_je, uint32_t *s_jn) {
-    // bit 31 flags an edge whose bitruss number is already known: it is never
-    // peeled again, so it needs no decrement
-    const bool fx = pr.x >> 31, fy = pr.y >> 31;
-    const uint32_t ex = pr.x & 0x7FFFFFFFu, ey = pr.y & 0x7FFFFFFFu;
+// Bloom phase of round r, N pair slots (died stamps d, members pr) of a bloom
+// with c pairs killed this round and bloom number kB at round start.  All the
+// slots' support decrements are issued before any result is examined, so they
+// travel together.
+template <uint32_t kSeg, uint32_t N>
+__device__ __forceinline__ void apply_slots(const PeelArgs &a, const uint32_t (&d)[N], const uint2 (&pr)[N],
+                                            uint32_t c, uint32_t kB, const Lvl &L, uint32_t round,
+                                            unsigned long long &upd, uint32_t *s_je, uint32_t *s_jn) {
     const uint32_t q = round + 1u;
-    const uint32_t dr = d >> 2;  // round of death (kAlive: 0x3FFFFFFF, no round)
-    if (d == kAlive || dr == q) {
-        // alive during this round (a pair killed for the next round still is):
-        // one butterfly lost per dead pair
-        if (!fx && decrement(a, ex, c, L)) join_next<kSeg>(a, ex, q, L.k, s_je, s_jn);
-        if (!fy && decrement(a, ey, c, L)) join_next<kSeg>(a, ey, q, L.k, s_je, s_jn);
-        upd += (fx ? 0 : 1) + (fy ? 0 : 1);
-    } else if (dr == round && kB > 1u) {
-        // died now: a member outside S (its bit not stamped) loses its
-        // k_B - 1 butterflies
-        const bool sx = fx || (d & 1u), sy = fy || (d & 2u);
-        if (!sx) {
-            if (decrement(a, ex, (long long)kB - 1, L)) join_next<kSeg>(a, ex, q, L.k, s_je, s_jn);
-            ++upd;
+    uint32_t e[2 * N];
+    long long dec[2 * N];
+#pragma unroll
+    for (uint32_t r = 0; r < N; ++r) {
+        // bit 31 flags an edge whose bitruss number is already known: it is
+        // never peeled again, so it needs no decrement
+        const bool fx = pr[r].x >> 31, fy = pr[r].y >> 31;
+        e[2 * r] = pr[r].x & 0x7FFFFFFFu;
+        e[2 * r + 1] = pr[r].y & 0x7FFFFFFFu;
+        dec[2 * r] = 0;
+        dec[2 * r + 1] = 0;
+        const uint32_t dr = d[r] >> 2;  // round of death (kAlive: 0x3FFFFFFF, no round)
+        if (d[r] == kAlive || dr == q) {
+            // alive during this round (a pair killed for the next round still
+            // is): one butterfly lost per dead pair
+            if (!fx) dec[2 * r] = c;
+            if (!fy) dec[2 * r + 1] = c;
+        } else if (dr == round && kB > 1u) {
+            // died now: a member outside S (its bit not stamped) loses its
+            // k_B - 1 butterflies
+            if (!(fx || (d[r] & 1u))) dec[2 * r] = (long long)kB - 1;
+            if (!(fy || (d[r] & 2u))) dec[2 * r + 1] = (long long)kB - 1;
         }
-        if (!sy) {
-            if (decrement(a, ey, (long long)kB - 1, L)) join_next<kSeg>(a, ey, q, L.k, s_je, s_jn);
-            ++upd;
-        }
+    }
+    long long old[2 * N];
+#pragma unroll
+    for (uint32_t i = 0; i < 2 * N; ++i)
+        old[i] = dec[i] ? (long long)atomicAdd(reinterpret_cast<unsigned long long *>(&a.sup[e[i]]),
+                                               (unsigned long long)(-dec[i]))
+                        : 0;
+#pragma unroll
+    for (uint32_t i = 0; i < 2 * N; ++i) {
+        if (!dec[i]) continue;
+        ++upd;
+        const long long now = old[i] - dec[i];
+        if (old[i] >= L.khi && now < L.khi) push_near(a, e[i], L.nq);
+        // exactly one decrement takes the edge from > k to <= k: it joins the
+        // next batch
+        if (old[i] > L.k && now <= L.k) join_next<kSeg>(a, e[i], q, L.k, s_je, s_jn);
     }
 }
 
@@ -665,9 +672,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                         d[r] = act ? __ldcg(&a.died[it.y + r]) : (round + 2u) << 2;  // inactive: no case applies
                         pr[r] = act ? a.pairs[it.y + r] : make_uint2(0, 0);
                     }
-#pragma unroll
-                    for (uint32_t r = 0; r < kSmall; ++r)
-                        apply_slot<kSeg>(a, d[r], pr[r], c, it.w, L, round, upd, s_je, &s_jn);
+                    apply_slots<kSeg, kSmall>(a, d, pr, c, it.w, L, round, upd, s_je, &s_jn);
                 }
                 unsigned big = __ballot_sync(kFull, cnt > kSmall);
                 while (big) {
@@ -685,9 +690,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                         d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : (round + 2u) << 2;
                         pr[r] = act ? a.pairs[p0 + 32u * r] : make_uint2(0, 0);
                     }
-#pragma unroll
-                    for (uint32_t r = 0; r < R; ++r)
-                        apply_slot<kSeg>(a, d[r], pr[r], bc, kB, L, round, upd, s_je, &s_jn);
+                    apply_slots<kSeg, R>(a, d, pr, bc, kB, L, round, upd, s_je, &s_jn);
                 }
             }
             // clear C of the blooms the previous round touched (threads from

@@ -179,6 +179,22 @@ def test_heavy_vertex_over_many_chunks(h):
     assert_parity(h, e, nU, nL)
 
 
+def test_start_vertex_with_2_16_lower_neighbours(h):
+    # a start vertex with at least 2^16 lower-ranked neighbours: its counter
+    # words cannot also count readers, so the count kernel clears them in a
+    # third walk and emit's place walk runs over the same 66k-arc vertex;
+    # three more upper vertices share 200 random neighbours each with it
+    rng = np.random.default_rng(11)
+    nU, nL = 4, 66000
+    rows = [(0, v) for v in range(nL)]
+    for w in range(1, nU):
+        rows += [(w, int(v)) for v in rng.choice(nL, 200, replace=False)]
+    e = np.array(rows, dtype=np.int32)
+    for flags in (0, bt.BT_TIE_LOWER_FIRST):
+        st = assert_parity(h, e, nU, nL, flags)
+        assert st["phi_max"] >= 100
+
+
 def test_isolated_vertices_and_single_edge(h):
     assert_parity(h, np.array([[3, 4]], np.int32), 10, 12)
     e = pins.biclique(3, 3, 5, 7)
@@ -252,7 +268,7 @@ def test_medium_vertex_sample_exact(h):
     assert_parity(h, g.edges, g.nU, g.nL)
 
 
-@pytest.mark.parametrize("join_cap,block_links", [(1, 2), (3, 16), (8, 64), (768, 2)])
+@pytest.mark.parametrize("join_cap,block_links", [(1, 2), (3, 16), (8, 64), (640, 2)])
 def test_overflow_paths_exact(h, join_cap, block_links):
     """The paths large graphs take, forced on small ones (bt_set_limits): a
     block that lists more joining edges than its cap lets the others queue
