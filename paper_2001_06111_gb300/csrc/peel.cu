@@ -674,23 +674,65 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     }
                     apply_slots<kSeg, kSmall>(a, d, pr, c, it.w, L, round, upd, s_je, &s_jn);
                 }
+                // items with many slots: the whole warp, one item at a time.
+                // With one slot a lane the next item's pair words are
+                // requested before this item's decrements go out (2M-edge
+                // graph 467 -> 460 ms, a C3-shaped 3M-edge graph 1534 ->
+                // 1481 ms); with two the extra registers spill and the
+                // 30M-edge graph measured 1 % slower, so items go one by one.
                 unsigned big = __ballot_sync(kFull, cnt > kSmall);
-                while (big) {
-                    const int src = __ffs(big) - 1;
-                    big &= big - 1u;
-                    const uint32_t bcnt = __shfl_sync(kFull, cnt, src);
-                    const uint32_t p0 = __shfl_sync(kFull, it.y, src) + lane;
-                    const uint32_t kB = __shfl_sync(kFull, it.w, src);
-                    const uint32_t bc = __shfl_sync(kFull, c, src);
-                    uint32_t d[R];
-                    uint2 pr[R];
-#pragma unroll
-                    for (uint32_t r = 0; r < R; ++r) {
-                        const bool act = lane + 32u * r < bcnt;
-                        d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : (round + 2u) << 2;
-                        pr[r] = act ? a.pairs[p0 + 32u * r] : make_uint2(0, 0);
+                uint32_t d[R], kB = 0, bc = 0;
+                uint2 pr[R];
+                if constexpr (R == 1) {
+                    if (big) {
+                        const int src = __ffs(big) - 1;
+                        big &= big - 1u;
+                        const uint32_t bcnt = __shfl_sync(kFull, cnt, src);
+                        const uint32_t p0 = __shfl_sync(kFull, it.y, src) + lane;
+                        kB = __shfl_sync(kFull, it.w, src);
+                        bc = __shfl_sync(kFull, c, src);
+                        const bool act = lane < bcnt;
+                        d[0] = act ? __ldcg(&a.died[p0]) : (round + 2u) << 2;
+                        pr[0] = act ? a.pairs[p0] : make_uint2(0, 0);
+                        for (;;) {
+                            const bool more = big != 0u;
+                            uint32_t dn = 0, kBn = 0, bcn = 0;
+                            uint2 prn = make_uint2(0, 0);
+                            if (more) {
+                                const int s2 = __ffs(big) - 1;
+                                big &= big - 1u;
+                                const uint32_t ncnt = __shfl_sync(kFull, cnt, s2);
+                                const uint32_t np0 = __shfl_sync(kFull, it.y, s2) + lane;
+                                kBn = __shfl_sync(kFull, it.w, s2);
+                                bcn = __shfl_sync(kFull, c, s2);
+                                const bool nact = lane < ncnt;
+                                dn = nact ? __ldcg(&a.died[np0]) : (round + 2u) << 2;
+                                prn = nact ? a.pairs[np0] : make_uint2(0, 0);
+                            }
+                            apply_slots<kSeg, R>(a, d, pr, bc, kB, L, round, upd, s_je, &s_jn);
+                            if (!more) break;
+                            d[0] = dn;
+                            pr[0] = prn;
+                            kB = kBn;
+                            bc = bcn;
+                        }
                     }
-                    apply_slots<kSeg, R>(a, d, pr, bc, kB, L, round, upd, s_je, &s_jn);
+                } else {
+                    while (big) {
+                        const int src = __ffs(big) - 1;
+                        big &= big - 1u;
+                        const uint32_t bcnt = __shfl_sync(kFull, cnt, src);
+                        const uint32_t p0 = __shfl_sync(kFull, it.y, src) + lane;
+                        kB = __shfl_sync(kFull, it.w, src);
+                        bc = __shfl_sync(kFull, c, src);
+#pragma unroll
+                        for (uint32_t r = 0; r < R; ++r) {
+                            const bool act = lane + 32u * r < bcnt;
+                            d[r] = act ? __ldcg(&a.died[p0 + 32u * r]) : (round + 2u) << 2;
+                            pr[r] = act ? a.pairs[p0 + 32u * r] : make_uint2(0, 0);
+                        }
+                        apply_slots<kSeg, R>(a, d, pr, bc, kB, L, round, upd, s_je, &s_jn);
+                    }
                 }
             }
             // clear C of the blooms the previous round touched (threads from
