@@ -264,15 +264,23 @@ __device__ __forceinline__ bool count_kill(const PeelArgs &a, uint32_t B, uint32
     return atomicAdd(&a.Cb[q % 3u][B], 1u) == 0u;
 }
 
-// An edge of the batch of round q kills pair p, of which it is member `side`
-// (0 first, 1 second).  The first edge to stamp the pair counts it (true);
-// a twin of the same batch adds its side bit to the stamp.
-__device__ __forceinline__ bool kill_pair(const PeelArgs &a, uint32_t p, uint32_t side, uint32_t q) {
-    const uint32_t bit = 1u << side;
-    const uint32_t old = atomicCAS(&a.died[p], kAlive, (q << 2) | bit);
-    if (old == kAlive) return true;
-    if ((old >> 2) == q) atomicOr(&a.died[p], bit);
-    return false;
+// Edges of the batch of round q kill the pairs of up to N links (won[r] set
+// on entry for the valid ones; link l[r] names the pair and which member the
+// edge is, 0 first, 1 second).  The first edge to stamp a pair counts it
+// (won[r] stays true); a twin of the same batch adds its side bit to the
+// stamp.  A lane's stamps go out together before any result is examined.
+template <uint32_t N>
+__device__ __forceinline__ void kill_pairs(const PeelArgs &a, const uint2 (&l)[N], bool (&won)[N], uint32_t q) {
+    uint32_t old[N];
+#pragma unroll
+    for (uint32_t r = 0; r < N; ++r)
+        old[r] = won[r] ? atomicCAS(&a.died[l[r].x], kAlive, (q << 2) | (1u << (l[r].y >> 31))) : 0u;
+#pragma unroll
+    for (uint32_t r = 0; r < N; ++r) {
+        if (!won[r]) continue;
+        won[r] = old[r] == kAlive;
+        if (!won[r] && (old[r] >> 2) == q) atomicOr(&a.died[l[r].x], 1u << (l[r].y >> 31));
+    }
 }
 
 // Whole warp (converged): each lane's pairs killed for round q (won[r], bloom
@@ -422,9 +430,11 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     uint32_t e = 0;
                     if (i < v_near) {
                         e = ldcg_u32(&a.near[L.nq][i]);
-                        if (ldcg_u32(&a.state[e]) == kAlive) {
+                        // state and support requested together
+                        const uint32_t stv = ldcg_u32(&a.state[e]);
+                        const unsigned long long sv = (unsigned long long)ldcg_ll(&a.sup[e]);
+                        if (stv == kAlive) {
                             keep = true;
-                            const unsigned long long sv = (unsigned long long)ldcg_ll(&a.sup[e]);
                             best = sv < best ? sv : best;
                         }
                     }
@@ -462,9 +472,10 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     uint32_t e = 0;
                     if (i < v_alive) {
                         e = ldcg_u32(&a.alive[ap][i]);
-                        if (ldcg_u32(&a.state[e]) == kAlive) {
+                        const uint32_t stv = ldcg_u32(&a.state[e]);
+                        const unsigned long long sv = (unsigned long long)ldcg_ll(&a.sup[e]);
+                        if (stv == kAlive) {
                             keep = true;
-                            const unsigned long long sv = (unsigned long long)ldcg_ll(&a.sup[e]);
                             best = sv < best ? sv : best;
                         }
                     }
@@ -538,11 +549,15 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     uint64_t ib = 0, ie = 0;
                     if (i < v_near) {
                         e = ldcg_u32(&a.near[L.nq][i]);
-                        if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k) {
+                        // state, support and link range requested together
+                        const uint32_t stv = ldcg_u32(&a.state[e]);
+                        const long long sv = ldcg_ll(&a.sup[e]);
+                        const uint64_t b0 = a.inc_off[e], b1 = a.inc_off[e + 1];
+                        if (stv == kAlive && sv <= L.k) {
                             join_batch(a, e, round, L.k);
                             ++sel;
-                            ib = a.inc_off[e];
-                            ie = a.inc_off[e + 1];
+                            ib = b0;
+                            ie = b1;
                             nseg = (uint32_t)((ie - ib + kSeg - 1) / kSeg);
                         }
                     }
@@ -564,9 +579,12 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             } else {
                 for (uint32_t i = gtid; i < v_near; i += nthreads) {
                     const uint32_t e = ldcg_u32(&a.near[L.nq][i]);
-                    if (ldcg_u32(&a.state[e]) == kAlive && ldcg_ll(&a.sup[e]) <= L.k) {
+                    const uint32_t stv = ldcg_u32(&a.state[e]);
+                    const long long sv = ldcg_ll(&a.sup[e]);
+                    const uint64_t b0 = a.inc_off[e], b1 = a.inc_off[e + 1];
+                    if (stv == kAlive && sv <= L.k) {
                         join_batch(a, e, round, L.k);
-                        push_items<kSeg>(a, e, par, a.inc_off[e], a.inc_off[e + 1]);
+                        push_items<kSeg>(a, e, par, b0, b1);
                         ++sel;
                     }
                 }
@@ -614,9 +632,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                         B[r] = l[r].y & 0x7FFFFFFFu;
                     }
                     // the first edge of the batch to stamp a pair kills it (once)
-#pragma unroll
-                    for (uint32_t r = 0; r < kSmall; ++r)
-                        if (won[r]) won[r] = kill_pair(a, l[r].x, l[r].y >> 31, round);
+                    kill_pairs<kSmall>(a, l, won, round);
                     warp_kills<kSeg, kSmall>(a, round, B, won, lane);
                 }
                 // items with many links: the whole warp, one item at a time
@@ -637,9 +653,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                         l[r] = won[r] ? a.inc[j0 + 32u * r] : make_uint2(0u, 0u);
                         B[r] = l[r].y & 0x7FFFFFFFu;
                     }
-#pragma unroll
-                    for (uint32_t r = 0; r < R; ++r)
-                        if (won[r]) won[r] = kill_pair(a, l[r].x, l[r].y >> 31, round);
+                    kill_pairs<R>(a, l, won, round);
                     warp_kills<kSeg, R>(a, round, B, won, lane);
                 }
             }
@@ -786,9 +800,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     B[r] = l[r].y & 0x7FFFFFFFu;
                 }
                 // the first edge of the batch to stamp a pair kills it (once)
-#pragma unroll
-                for (uint32_t r = 0; r < 2; ++r)
-                    if (won[r]) won[r] = kill_pair(a, l[r].x, l[r].y >> 31, q);
+                kill_pairs<2>(a, l, won, q);
                 warp_kills<kSeg, 2>(a, q, B, won, lane);
                 if (threadIdx.x == 0) s_jn = 0;
             }
