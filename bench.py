@@ -41,6 +41,10 @@ WORKLOADS = {
                    gammaL=2.4, cap=20000, seed=2),
     "small": dict(name="chunglu-2k-1.5k-20k", nU=2000, nL=1500, m=20000, gammaU=2.2, gammaL=2.5,
                   cap=0, seed=1),
+    # the shape of "large" at a tenth of its edges: small enough for ncu
+    # captures of the peel, whose DRAM traffic is scaled to the full workload
+    "c3shape": dict(name="chunglu-200k-50k-3M-planted20", nU=200000, nL=50000, m=3000000, gammaU=2.0,
+                    gammaL=2.3, cap=0, seed=33, nplant=20, plant_lo=50, plant_hi=300, plant_p=0.9),
     "batch": dict(name="batch-4096-chunglu-logU(100,200000)", graphs=4096),
     "serve": dict(name="poisson-serve-batchdist+5%-2M", pool=256, big=4,
                   rates=[50, 100, 200, 500, 1000, 2000], seconds=60.0),
@@ -55,8 +59,8 @@ UNIT = "edges/s"
 # vertex-induced samples (the sampling of Section VI's scalability study) the
 # CPU oracle decomposes: the baseline leg (one sample) and the reference arm
 # (one sample per step), sized to a few to tens of seconds of oracle time
-CPU_SAMPLE_FRAC = {"large": 0.07, "medium": 0.3, "small": 1.0}
-REF_SAMPLE_FRAC = {"large": 0.04, "medium": 0.2, "small": 1.0}
+CPU_SAMPLE_FRAC = {"large": 0.07, "medium": 0.3, "small": 1.0, "c3shape": 0.2}
+REF_SAMPLE_FRAC = {"large": 0.04, "medium": 0.2, "small": 1.0, "c3shape": 0.1}
 
 
 def gen_workload(w):
@@ -205,7 +209,8 @@ def measured_traffic(kernel: str, workload: str, alg_bytes=None):
     return int(m_t.group(1))
 
 
-WORKLOAD_PROFILE_TAG = {"large": "c3shape-3M", "medium": "chunglu-2M", "small": "chunglu-20k"}
+WORKLOAD_PROFILE_TAG = {"large": "c3shape-3M", "c3shape": "c3shape-3M", "medium": "chunglu-2M",
+                        "small": "chunglu-20k"}
 
 
 def run_reference(args):
@@ -597,8 +602,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 2M-edge and 4,096-graph entries of the default line")
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
-                    help="large (default) is the benchmark workload; medium and small are the "
-                         "other single-graph workloads; batch, serve and updates print their own lines")
+                    help="large (default) is the benchmark workload; medium, small and c3shape "
+                         "(large's shape at 3M edges) are the other single-graph workloads; batch, "
+                         "serve and updates print their own lines")
     ap.add_argument("--rates", default="",
                     help="serve workload: comma-separated arrival rates (req/s) instead of the full sweep")
     ap.add_argument("--seconds", type=float, default=0.0,
