@@ -226,11 +226,12 @@ int bt_profile_read(const bt_handle *h, bt_profile *out);
  *   fail_alloc_at:      n > 0: inside each call, device allocation number n
  *                       (counted from 1) fails as if the device were out of
  *                       memory; the call returns BT_ERR_NOMEM.
- *   join_cap:           n > 0: a peel block lists at most n (instead of 640)
+ *   join_cap:           n > 0: a peel block lists at most n (instead of its
+ *                       thread count: 640, or 512 with 128-entry items)
  *                       of the edges that join the next batch during its
  *                       bloom phase; the others queue their own links.
  *   block_links:        n > 0: a peel block's kill stage handles at most n
- *                       (instead of 1,280) links itself; longer lists become
+ *                       (instead of two a thread) links itself; longer lists become
  *                       incidence items.  (These two change no result; they
  *                       make small graphs take the paths large ones take.)
  * limits == NULL restores every default.  Errors: BT_ERR_ARG (h NULL).
@@ -291,7 +292,7 @@ typedef struct {
 typedef struct {
     uint64_t max_edges_per_launch;  /* graphs are packed into unions of at most this many edges */
     uint32_t count_threads;         /* wedge-count / index block size: 256, 512 or 1024 */
-    uint32_t peel_item;             /* peel work item: 32 or 64 links / pair slots per warp */
+    uint32_t peel_item;             /* peel work item: 32, 64 or 128 links / pair slots per warp */
     uint32_t reserved[2];
 } bt_tune;
 

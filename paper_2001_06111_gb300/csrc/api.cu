@@ -604,11 +604,12 @@ int bt_decompose(bt_handle *h, const int32_t *edges, uint64_t m, uint32_t nU, ui
     rc = build_index_impl(h, edges, m, nU, nL, flags, s_int, al);
     bt::PeelResult pr;
     if (rc == BT_OK) {
-        // work items of 64 pair slots (two per lane) pay off when rounds are
-        // heavy: on the 30M-edge planted graph (3.1e9 twin pairs) the peel
-        // took 22.0 s against 24.6 s with 32; on graphs with up to 2e8 pairs
-        // 32 measured 3-8 % faster
-        const int seg = h->index.w2 > (1ull << 30) ? 64 : h->peel_seg;
+        // larger work items pay off when rounds are heavy: on the 30M-edge
+        // planted graph (3.1e9 twin pairs) the peel took 18.1 s with 128
+        // pair slots an item (four a lane, 512-thread blocks), 18.6 s with 64
+        // and 21.9 s with 32; on graphs with up to 2e8 pairs 32 measured
+        // 3-8 % faster than 64
+        const int seg = h->index.w2 > (1ull << 30) ? 128 : h->peel_seg;
         cudaError_t e = bt::peel(h->index, s_int, p_int, pr, peel_sms(h), al, seg);
         if (e == cudaSuccess) e = bt::gather_u64(s_int, h->index.newid, d_sup, m, al);
         if (e == cudaSuccess) e = bt::gather_u32(p_int, h->index.newid, d_phi, m, al);

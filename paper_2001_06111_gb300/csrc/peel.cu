@@ -50,20 +50,22 @@
 namespace bt {
 namespace {
 
-constexpr int kPeelThreads = 640;  // 96 registers a thread, no spills in either instantiation
-// entries per work item: SEG = 32 or 64 (template parameter picked by the
-// batch autotuner); each lane handles SEG / 32 entries with their loads and
-// atomics issued together.
+// entries per work item: SEG = 32, 64 or 128 (template parameter: 32 or 64
+// picked by the batch autotuner, 128 for indexes of over 2^30 twin pairs);
+// each lane handles SEG / 32 entries with their loads and atomics issued
+// together.  Threads a block: 640 (96 registers, no spills) for 32- and
+// 64-entry items, 512 (128 registers) for 128-entry items, whose four slots
+// a lane need the registers.
+__host__ __device__ constexpr int peel_threads(uint32_t seg) { return seg == 128 ? 512 : 640; }
 // items with at most kSmall entries are processed by one lane each, larger
 // ones by the whole warp.  Lane l of warp w takes item w + l * nwarps (plus
 // multiples of 32 * nwarps): a round with fewer items than warps still gives
 // every item its own warp, and a large round fills all lanes.
 constexpr uint32_t kSmall = 2;
 // edges that join the next batch in a bloom phase are listed per block (up to
-// kJoinCap); the block kills their twin pairs at the end of the phase, two
-// links per thread, for the edges whose links fit in the first kBlockLinks
-constexpr uint32_t kJoinCap = kPeelThreads;
-constexpr uint32_t kBlockLinks = 2 * kPeelThreads;
+// one per thread); the block kills their twin pairs at the end of the phase,
+// two links per thread, for the edges whose links fit in the first two per
+// thread
 constexpr unsigned long long kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;  // 20 s (default)
 // pair death stamps: round << 2 | (first member in the batch) | (second << 1);
 // kAlive (all ones) is never a stamp while rounds stay below kMaxRounds
@@ -119,8 +121,8 @@ struct PeelArgs {
     uint64_t round_limit;
     unsigned long long barrier_timeout_ns;
     unsigned long long hold_barrier;  // 0, or n: block 0 skips its arrival at barrier n (from 1)
-    uint32_t join_cap;     // edges a block lists in a bloom phase (<= kJoinCap)
-    uint32_t block_links;  // links of the listed edges the block stage kills itself (<= kBlockLinks)
+    uint32_t join_cap;     // edges a block lists in a bloom phase (<= threads a block)
+    uint32_t block_links;  // links of the listed edges the block stage kills itself (<= 2 a thread)
     // progressive compression: peel only the m_active unassigned edges, start
     // at level k_init, and record phi only for levels >= assign_from
     uint64_t m_active;
@@ -382,8 +384,10 @@ __device__ __forceinline__ void apply_slots(const PeelArgs &a, const uint32_t (&
 }
 
 template <uint32_t kSeg>
-__global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
+__global__ void __launch_bounds__(peel_threads(kSeg), 1) k_peel(PeelArgs a) {
     constexpr uint32_t R = kSeg / 32;  // entries per lane
+    constexpr uint32_t kT = peel_threads(kSeg);
+    constexpr uint32_t kJoinCap = kT;
     const int lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -787,7 +791,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 bool won[2];
 #pragma unroll
                 for (uint32_t r = 0; r < 2; ++r) {
-                    const uint32_t x = threadIdx.x + r * (uint32_t)kPeelThreads;
+                    const uint32_t x = threadIdx.x + r * kT;
                     won[r] = false;
                     l[r] = make_uint2(0u, 0u);
                     if (x < lim) {
@@ -863,7 +867,9 @@ inline unsigned grid_for(uint64_t items, int threads, unsigned cap) {
 
 cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, PeelResult &res,
                  int num_sms, Alloc &al, int seg, const PeelOpts *opts) {
-    const uint32_t kSeg = seg == 64 ? 64u : 32u;
+    const uint32_t kSeg = seg == 128 ? 128u : seg == 64 ? 64u : 32u;
+    const uint32_t kT = (uint32_t)peel_threads(kSeg);
+    const uint32_t kJoinCap = kT, kBlockLinks = 2 * kT;
     const uint64_t m = ix.m;
     res = PeelResult{};
     if (m == 0 || (opts && opts->assigned && opts->m_active == 0)) return cudaSuccess;
@@ -923,10 +929,10 @@ cudaError_t peel(const Index &ix, const uint64_t *support, uint32_t *phi_out, Pe
     h.minsup2 = ~0ull;
     BT_CUDA(cudaMemcpyAsync(a.ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     int bps = 0;
-    void *kfn = kSeg == 64 ? (void *)k_peel<64> : (void *)k_peel<32>;
-    BT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, kPeelThreads, 0));
+    void *kfn = kSeg == 128 ? (void *)k_peel<128> : kSeg == 64 ? (void *)k_peel<64> : (void *)k_peel<32>;
+    BT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, (int)kT, 0));
     if (bps < 1) return cudaErrorCooperativeLaunchTooLarge;
-    dim3 grid((unsigned)(num_sms * bps)), block(kPeelThreads);
+    dim3 grid((unsigned)(num_sms * bps)), block(kT);
     void *kargs[] = {&a};
     BT_CUDA(cudaLaunchCooperativeKernel(kfn, grid, block, kargs, 0, st));
     al.launches++;

@@ -107,6 +107,23 @@ def test_batch_reports_bad_graph(h):
     assert len(outs) == 4
 
 
+def test_128_entry_peel_items_exact(h):
+    # 128-entry peel items (four slots a lane, 512-thread blocks) run on
+    # indexes of over 2^30 twin pairs; forced here on graphs whose planted
+    # dense bicliques give blooms of many pairs, against the oracle
+    planted = [synth.chunglu(2000, 1500, 20000, 2.2, 2.5, seed=7, nplant=6, plant_lo=10, plant_hi=40,
+                             plant_p=0.9),
+               synth.chunglu(5000, 3000, 60000, 2.0, 2.3, seed=9, nplant=10, plant_lo=20, plant_hi=80,
+                             plant_p=0.9)]
+    gs = [(g.edges, g.nU, g.nL) for g in planted] + [(pins.biclique(40, 50), 40, 50)]
+    outs, st = bt.bt_decompose_batch(h, gs, count_threads=512, peel_item=128)
+    assert st["peel_item"] == 128
+    for (e, nU, nL), (sup, phi) in zip(gs, outs):
+        s0, p0 = oracle.bitruss(e, nU, nL)
+        np.testing.assert_array_equal(sup, s0)
+        np.testing.assert_array_equal(phi.astype(np.uint64), p0)
+
+
 def test_autotuner_choice_cached_and_schedules_exact(h):
     gs = mixed_graphs()
     h2 = bt.bt_create(0)
@@ -118,7 +135,7 @@ def test_autotuner_choice_cached_and_schedules_exact(h):
     assert st1["tuned"] == 1 and st2["tuned"] == 2
     assert st1["count_threads"] in (256, 512, 1024) and st1["peel_item"] in (32, 64)
     assert (st1["count_threads"], st1["peel_item"]) == (st2["count_threads"], st2["peel_item"])
-    for nt, seg in ((256, 64), (1024, 32), (512, 64)):
+    for nt, seg in ((256, 64), (1024, 32), (512, 64), (512, 128)):
         forced, st = bt.bt_decompose_batch(h, gs, count_threads=nt, peel_item=seg)
         assert st["tuned"] == 0 and (st["count_threads"], st["peel_item"]) == (nt, seg)
         for (s0, p0), (s1, p1) in zip(first, forced):
