@@ -70,3 +70,16 @@ def test_committed_summary_names_both_sources():
     text = open(os.path.join(bench.ROOT, "profiles", "k_peel-chunglu-2M.md")).read()
     assert "sha256 (csrc/peel.cu)" in text and "sha256 (csrc/csr.cu)" in text
     assert "traffic_bytes_per_launch" in text
+
+
+def test_c3shape_workload_is_the_scaled_capture():
+    # the 3M-edge workload whose capture is scaled to the 30M-edge graph: its
+    # own traffic is the capture itself (ratio one), and it has the large
+    # graph's generator parameters at a tenth of the edges
+    w, big = bench.WORKLOADS["c3shape"], bench.WORKLOADS["large"]
+    assert w["m"] * 10 == big["m"]
+    for key in ("gammaU", "gammaL", "plant_lo", "plant_hi", "plant_p"):
+        assert w[key] == big[key]
+    assert bench.WORKLOAD_PROFILE_TAG["c3shape"] == bench.WORKLOAD_PROFILE_TAG["large"]
+    text = open(os.path.join(bench.ROOT, "profiles", "k_peel-c3shape-3M.md")).read()
+    assert "--workload c3shape" in text
