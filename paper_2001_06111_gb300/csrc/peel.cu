@@ -295,11 +295,34 @@ __device__ __forceinline__ void warp_kills(const PeelArgs &a, uint32_t q, const 
                                            const bool (&won)[N], int lane) {
     uint32_t bo0[N], span[N], kB[N], nseg[N];
     uint32_t mine = 0;
+    if constexpr (N >= 4) {
+        // four kills a lane: their bloom loads, then their count atomics, go
+        // out together
+        uint32_t prev[N];
 #pragma unroll
-    for (uint32_t r = 0; r < N; ++r) {
-        nseg[r] = 0;
-        if (won[r] && count_kill(a, B[r], q, bo0[r], span[r], kB[r])) nseg[r] = (span[r] + kSeg - 1) / kSeg;
-        mine += nseg[r];
+        for (uint32_t r = 0; r < N; ++r) {
+            if (won[r]) {
+                bo0[r] = a.bloom_off[B[r]];
+                span[r] = a.bloom_off[B[r] + 1] - bo0[r];
+                const unsigned long long w = __ldcg(&a.bw[B[r]]);
+                const uint32_t cprev = __ldcg(&a.Cb[(q + 2u) % 3u][B[r]]);  // C_{q-1}(B)
+                kB[r] = (uint32_t)(w >> 32) == q - 1u ? (uint32_t)w : (uint32_t)w - cprev;
+            }
+        }
+#pragma unroll
+        for (uint32_t r = 0; r < N; ++r) prev[r] = won[r] ? atomicAdd(&a.Cb[q % 3u][B[r]], 1u) : 1u;
+#pragma unroll
+        for (uint32_t r = 0; r < N; ++r) {
+            nseg[r] = prev[r] == 0u ? (span[r] + kSeg - 1) / kSeg : 0u;
+            mine += nseg[r];
+        }
+    } else {
+#pragma unroll
+        for (uint32_t r = 0; r < N; ++r) {
+            nseg[r] = 0;
+            if (won[r] && count_kill(a, B[r], q, bo0[r], span[r], kB[r])) nseg[r] = (span[r] + kSeg - 1) / kSeg;
+            mine += nseg[r];
+        }
     }
     const uint32_t incl = dev::warp_incl_scan(mine);
     const uint32_t all = __shfl_sync(kFull, incl, 31);
